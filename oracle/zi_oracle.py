@@ -199,15 +199,27 @@ def element_stiffness(grads: np.ndarray, vol: np.ndarray, sigma6: np.ndarray) ->
     return vol[:, None, None] * np.einsum("mai,mij,mbj->mab", grads, S, grads)
 
 
-def assemble_stiffness(n: int, tets: np.ndarray, Ke: np.ndarray) -> sp.csr_matrix:
-    """A_vol = sum_e K_e scattered on the mesh-graph pattern (explicit zeros
-    are kept so the pattern does not depend on sigma)."""
+def stiffness_triplets(tets: np.ndarray, Ke: np.ndarray):
+    """(rows, cols, values) of every element contribution K_e[a, b]."""
     rows = np.repeat(tets, 4, axis=1).ravel()
     cols = np.tile(tets, (1, 4)).ravel()
-    A = sp.coo_matrix((Ke.reshape(-1), (rows, cols)), shape=(n, n)).tocsr()
+    return rows, cols, Ke.reshape(-1)
+
+
+def csr_from_triplets(n: int, rows, cols, vals) -> sp.csr_matrix:
+    """Sum of the triplets on their union pattern.  COO -> CSR conversion sums
+    duplicates and keeps explicit zeros, so the pattern is the mesh graph
+    whatever the values (sparse matrix *addition* would drop exact zeros)."""
+    A = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
     A.sum_duplicates()
     A.sort_indices()
     return A
+
+
+def assemble_stiffness(n: int, tets: np.ndarray, Ke: np.ndarray) -> sp.csr_matrix:
+    """A_vol = sum_e K_e scattered on the mesh-graph pattern (explicit zeros
+    are kept so the pattern does not depend on sigma)."""
+    return csr_from_triplets(n, *stiffness_triplets(tets, Ke))
 
 
 # ---------------------------------------------------------------------------
@@ -258,8 +270,8 @@ def point_electrode_nodes(nodes, bfaces, centres):
 
 
 def cem_terms(n, nodes, bfaces, tri, el, z, n_el):
-    """A_cem (sparse), B (n x L dense), C (L,) for the complete electrode
-    model with z_l = Z_l * |e_l|:
+    """A_cem (triplets rows, cols, values), B (n x L dense), C (L,) for the
+    complete electrode model with z_l = Z_l * |e_l|:
         A_cem[i,j] = sum_l 1/z_l int_{e_l} psi_i psi_j   (P1 surface mass,
                      area/12 * (2 on the diagonal, 1 off it))
         B[i,l]     = 1/z_l int_{e_l} psi_i              (area/3 per vertex)
@@ -272,8 +284,7 @@ def cem_terms(n, nodes, bfaces, tri, el, z, n_el):
         for b in range(3):
             rows.append(t[:, a]); cols.append(t[:, b])
             vals.append(w * area / 12.0 * (2.0 if a == b else 1.0))
-    A_cem = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                          shape=(n, n)).tocsr()
+    A_cem = (np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
     B = np.zeros((n, n_el))
     for a in range(3):
         np.add.at(B, (t[:, a], el), w * area / 3.0)
@@ -363,14 +374,15 @@ class System:
         self.mesh, self.n, self.mode = mesh, n, model
         self.grads, self.vol = element_geometry(nodes, tets)
         self.Ke = element_stiffness(self.grads, self.vol, sigma6)
-        A = assemble_stiffness(n, tets, self.Ke)
+        r, c, v = stiffness_triplets(tets, self.Ke)
+        A = csr_from_triplets(n, r, c, v)
         self.n_el = centres.shape[0]
         if model == "cem":
             z = np.asarray(z, dtype=np.float64)
             self.tri, self.el = electrode_patches(nodes, bfaces, centres, radius)
-            A_cem, B, C = cem_terms(n, nodes, bfaces, self.tri, self.el, z, self.n_el)
-            A = (A + A_cem).tocsr()
-            A.sum_duplicates(); A.sort_indices()
+            (rc, cc, vc), B, C = cem_terms(n, nodes, bfaces, self.tri, self.el, z, self.n_el)
+            A = csr_from_triplets(n, np.concatenate([r, rc]), np.concatenate([c, cc]),
+                                  np.concatenate([v, vc]))
             self.ip = ground_node_cem(bfaces, self.tri)
             self.B_unpinned = B.copy()
             B[self.ip, :] = 0.0

@@ -493,3 +493,20 @@ def test_average_reference_matrix():
     assert np.max(np.abs(R @ np.ones(L))) < 1e-15
     v = np.arange(L, dtype=float) ** 2
     assert np.allclose(R @ v, v - v.mean())
+
+
+def test_pattern_is_the_mesh_graph_whatever_the_values():
+    """The CSR pattern of A (with CEM terms) is {(i, j): i, j share a tet},
+    independent of sigma: an isotropic sigma (exactly-zero couplings on the
+    Kuhn diagonals of exact coordinates) gives the same pattern."""
+    spec, mesh, s6, sysm, _, _ = _small_system(h=0.25, aniso=False)
+    tets = mesh["tets"]
+    pairs = set()
+    for t in tets:
+        for a in t:
+            for b in t:
+                pairs.add((int(a), int(b)))
+    A = sysm.A_unpinned
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    got = set(zip(rows.tolist(), A.indices.tolist()))
+    assert got == pairs
