@@ -1,0 +1,318 @@
+"""Lead-field build benchmark on GB300.
+
+One step = one whole LF build of the three-shell head at h = 2 mm
+(428,185 nodes, 2,447,424 tets, 128 complete-model electrodes, 20,000
+dipoles x 3 orientations): dipole location, assembly (element stiffness,
+pattern, CEM terms, grounding), T = A^-1 B by multi-RHS PCG to a relative
+residual of 1e-10 per column, source application and the electrode Schur
+step, from inputs resident in HBM to L (128 x 60,000) in HBM.
+
+The headline is the mixed-precision build (FP32 inner PCG inside FP64
+iterative refinement); the plain FP64 PCG build on the same GPU is reported
+beside it, with the relative difference of the two lead fields.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas:
+each rank builds the same lead field (no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "LF build s, mixed vs FP64 PCG at rel.err<=1e-6 on 1 GB300; SpMM HBM GB/s vs peak"
+UNIT = "s"
+WORKLOAD = "three-shell sphere 80/86/92 mm, h=2 mm Kuhn grid (428185 nodes, 2447424 tets), " \
+           "128 CEM electrodes r=5 mm z=2e-3 Ohm m^2, 20000 dipoles x 3, PCG tol 1e-10"
+# ncu DRAM traffic per launch of the FP32 SpMM on this workload, from the capture
+# summarised in profiles/ (None until taken, or once the kernel source changed).
+SPMM_TRAFFIC = {"source_sha": None, "bytes": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison build")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--h", type=float, default=0.002, help="grid step (m) of the timed workload")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (the baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+ORACLE_SAMPLE = dict(h=0.004, electrodes=128, dipoles=20000)
+ORACLE_SAMPLE_TEXT = ("oracle LF build (numpy + SuperLU direct solve, 1 thread) of the same three-shell head, "
+                      "128 CEM electrodes and 20000 dipoles at h=4 mm (56235 nodes): the h=2 mm direct "
+                      "factorisation does not fit a bounded CPU sample")
+
+
+def oracle_once() -> float:
+    """One oracle LF build of the sample, in a fresh single-threaded process
+    (spawned with exec, so it never inherits a CUDA context)."""
+    code = ("import sys,time; sys.path.insert(0, %r)\n"
+            "from oracle import zi_oracle as O\n"
+            "from paper_1811_07717_gb300 import workloads as W\n"
+            "spec = W.three_shell(%r, %d, %d, seed=2)\n"
+            "t = time.perf_counter(); O.leadfield_from_spec(spec, W); print(time.perf_counter() - t)\n"
+            % (ROOT, ORACLE_SAMPLE["h"], ORACLE_SAMPLE["electrodes"], ORACLE_SAMPLE["dipoles"]))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-500:])
+    return float(r.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_once()
+    ts = [oracle_once() for _ in range(max(1, args.steps))]
+    v = statistics.mean(ts)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": ORACLE_SAMPLE_TEXT},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE_TEXT},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6800.0, "of fallback"
+
+
+def spmm_source_sha():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1811_07717_gb300", "csrc", "zi_pcg.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    from paper_1811_07717_gb300 import workloads as W
+    from paper_1811_07717_gb300 import _build, zi
+    _build.build()
+
+    spec = W.three_shell(args.h, 128, 20000, seed=2)
+    dev = torch.device("cuda", local)
+    mesh = zi.mesh_from_grid(spec.h, spec.radii)
+    s6 = W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(), mesh["labels"].cpu().numpy())
+    centres, z = W.electrode_inputs(spec)
+    pos, q = W.dipole_inputs(spec)
+    d = dict(nodes=mesh["nodes"], tets=mesh["tets"], bfaces=mesh["bfaces"],
+             s6=torch.from_numpy(s6).to(dev), centres=torch.from_numpy(centres).to(dev),
+             z=torch.from_numpy(z).to(dev), pos=torch.from_numpy(pos).to(dev))
+    torch.cuda.synchronize()
+
+    def lf_build(opts):
+        dip = zi.locate_dipoles_grid(spec.h, spec.radii, d["pos"])
+        system = zi.System(d["nodes"], d["tets"], d["s6"], d["bfaces"], d["centres"], model="cem", z=d["z"],
+                           radius=spec.electrode_radius)
+        L = system.leadfield(dip, opts)
+        system.close()
+        return L
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(opts, warmup, steps):
+        for _ in range(warmup):
+            L = lf_build(opts)
+        barrier()
+        l0 = zi.kernel_launches()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(torch.cuda.current_device()) as clk:
+            t0.record()
+            for _ in range(steps):
+                L = lf_build(opts)
+            t1.record()
+            barrier()
+        launches = zi.kernel_launches() - l0
+        sec = t0.elapsed_time(t1) / 1e3 / steps
+        if dist is not None:
+            tt = torch.tensor([sec], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            sec = float(tt.item())
+        return sec, L, launches, clk.summary()
+
+    mixed = zi.SolverOpts(tol=1e-10, precision=zi.MIXED)
+    fp64 = zi.SolverOpts(tol=1e-10, precision=zi.FP64)
+    sec_mixed, L_mixed, launches, clocks = timed(mixed, args.warmup, args.steps)
+
+    extra = {}
+    if not args.no_fp64:
+        sec64, L64, _, clocks64 = timed(fp64, 1, 1)
+        diff = float(torch.linalg.norm(L_mixed - L64) / torch.linalg.norm(L64))
+        extra = {"fp64_lf_build_s": sec64, "speedup_mixed_vs_fp64": sec64 / sec_mixed,
+                 "mixed_vs_fp64_rel_frobenius": diff, "fp64_clocks": clocks64}
+        del L64
+
+    # iteration counts and the SpMM roofline on one more build
+    system = zi.System(d["nodes"], d["tets"], d["s6"], d["bfaces"], d["centres"], model="cem", z=d["z"],
+                       radius=spec.electrode_radius)
+    _, it_mixed, rr_mixed = system.transfer(mixed, want_T=False)
+    ms32, bytes32 = system.time_spmm(zi.MIXED, reps=5)
+    system.close()
+    peak, peak_note = measured_peak_gbs()
+    achieved = bytes32 / (ms32 * 1e-3) / 1e9
+    traffic = SPMM_TRAFFIC["bytes"] if SPMM_TRAFFIC["source_sha"] == spmm_source_sha() else None
+    roofline = {"bound": "hbm", "kernel": "k_spmm_dot<float> (FP32 SpMM fused with column dots)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_note": peak_note, "traffic": traffic, "algorithmic_bytes": bytes32,
+                "ms_per_launch": ms32}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = {k: v.cpu().pin_memory() for k, v in d.items()}
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+
+        def e2e_build():
+            dd = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+            dip = zi.locate_dipoles_grid(spec.h, spec.radii, dd["pos"])
+            system = zi.System(dd["nodes"], dd["tets"], dd["s6"], dd["bfaces"], dd["centres"], model="cem",
+                               z=dd["z"], radius=spec.electrode_radius)
+            L = system.leadfield(dip, mixed).cpu()
+            system.close()
+            return L
+        e2e_build()
+        barrier()
+        t = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            Lh = e2e_build()
+        barrier()
+        e2e_sec = (time.perf_counter() - t) / max(1, args.steps)
+        e2e = {"value": e2e_sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(Lh.numel() * Lh.element_size())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            cpu_s = oracle_once()
+            cpu = {"value": cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE_TEXT}
+        except Exception as ex:  # reported, never silently replaced
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %s" % ex}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": sec_mixed, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": sec_mixed * 1e3, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner PCG / f64 refinement, assembly, LF",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_nodes": int(d["nodes"].shape[0]),
+                           "n_tets": int(d["tets"].shape[0]), "electrodes": 128, "dipoles": 20000,
+                           "precision": "mixed", "l2": "inputs larger than L2 (T alone is 438 MB)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "iterations_mixed_max": int(it_mixed.max()), "relres_mixed_max": float(rr_mixed.max()),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

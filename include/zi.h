@@ -1,0 +1,270 @@
+/*
+ * zi.h -- C ABI of libzi, a GB300 (sm_103a) implementation of the finite-element
+ * lead-field (LF) build of the Zeffiro Interface paper (arXiv 1811.07717):
+ * tetrahedral P1 stiffness assembly with per-element conductivity tensors,
+ * complete-electrode-model (CEM) terms, the transfer matrix T = A^-1 B by
+ * multi-right-hand-side preconditioned conjugate gradients, the EEG lead field
+ * L = R (C - B^T T)^-1 T^T F and the linearised-EIT Jacobian.
+ *
+ * Conventions for every entry point
+ *   - Plain C: no exceptions cross this boundary; every call returns a zi_status
+ *     (0 = ZI_OK).  zi_last_error() gives the message of the last failure of the
+ *     calling thread.
+ *   - Arrays are row-major, indices are 0-based int32, sizes int64.
+ *   - "device" pointers are CUDA global-memory pointers of the current device;
+ *     "host" pointers are ordinary host memory.  The caller owns every buffer it
+ *     passes; outputs are written, never reallocated.  A zi_system handle owns
+ *     only library-internal memory and is released by zi_system_destroy().
+ *   - Every call that launches GPU work takes a cudaStream_t (0 = legacy default
+ *     stream) and is stream-ordered: device outputs are valid once that stream
+ *     reaches the point of the call.  Calls that return a size or a status read
+ *     back from the device synchronise the stream before returning.
+ *   - Units: SI (m, S/m, Ohm*m^2).  Any consistent length unit works for the
+ *     mesh calls; conductivity and contact impedance scale as usual.
+ *
+ * Error behaviour: ZI_ERR_ARG for null pointers, negative or inconsistent sizes
+ * and unsupported options; ZI_ERR_BAD_MESH for a non-positive element volume, an
+ * electrode with no surface patch, overlapping patches, two point electrodes on
+ * one node or a dipole outside the mesh; ZI_ERR_NONFINITE for NaN/Inf inputs;
+ * ZI_ERR_NOT_CONVERGED when a column misses its tolerance within maxit (outputs
+ * are still written; per-column iteration counts and residuals say which);
+ * ZI_ERR_TIMEOUT when a device-side wait exceeded its bound; ZI_ERR_CUDA for a
+ * CUDA runtime failure; ZI_ERR_NOMEM when device memory runs out.
+ */
+#ifndef ZI_H
+#define ZI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#ifndef __CUDA_RUNTIME_H__
+typedef struct CUstream_st* cudaStream_t;
+#endif
+
+typedef enum zi_status {
+  ZI_OK = 0,
+  ZI_ERR_ARG = 1,
+  ZI_ERR_BAD_MESH = 2,
+  ZI_ERR_NONFINITE = 3,
+  ZI_ERR_NOT_CONVERGED = 4,
+  ZI_ERR_TIMEOUT = 5,
+  ZI_ERR_CUDA = 6,
+  ZI_ERR_NOMEM = 7
+} zi_status;
+
+/* Electrode models. */
+enum { ZI_ELECTRODE_POINT = 0, ZI_ELECTRODE_CEM = 1 };
+/* Diagonal preconditioners (Sec. 2.3.1): Jacobi 1/a_ii, or the paper's lumped
+ * diagonal preconditioner 1/sum_j |a_ij|. */
+enum { ZI_PRECOND_JACOBI = 0, ZI_PRECOND_LDP = 1 };
+/* Solver precision: FP64 throughout, or FP32 inner PCG inside FP64 iterative
+ * refinement (FP64 residual b - A x and solution update). */
+enum { ZI_FP64 = 0, ZI_MIXED = 1 };
+/* EIT output modes. */
+enum { ZI_EIT_FULL = 0, ZI_EIT_VJP = 1 };
+
+typedef struct zi_system zi_system;
+
+/* Version of this ABI (major*10000 + minor*100 + patch). */
+int zi_version(void);
+
+/* Copies the message of the calling thread's last error (NUL-terminated,
+ * truncated to len) into buf; returns the status of that error. */
+int zi_last_error(char* buf, size_t len);
+
+/* Short name of a status code ("ZI_OK", ...). Static storage. */
+const char* zi_status_string(int status);
+
+/* ------------------------------------------------------------------------ */
+/* Mesh (stand-in for the paper's mesh tool, Sec. 2.5; the mesh fields are    */
+/* the zef.nodes / zef.tetra arrays of Sec. 2.5)                              */
+/* ------------------------------------------------------------------------ */
+
+/* Regular-grid Kuhn mesh of the ball r < radii[n_shells-1].
+ *   Grid indices run over [-N, N] per axis, N = ceil(R_out/h) + 1.  Cube
+ *   (i,j,k) spans [i,i+1]h x [j,j+1]h x [k,k+1]h and is kept when
+ *   (2i+1)^2 + (2j+1)^2 + (2k+1)^2 < (2R_out/h)^2 (its centre is inside); its
+ *   label is the first shell s with the same test against radii[s] true.
+ *   Nodes: corners of kept cubes, ordered by grid linear index; coordinates
+ *   (i*h, j*h, k*h) in FP64.  Tets: kept cubes in grid order, six Kuhn tets per
+ *   cube for the axis permutations in lexicographic order, path
+ *   v0 -> v0+e_a -> v0+e_a+e_b -> v0+(1,1,1), last two vertices swapped when
+ *   that path is negatively oriented.  Boundary faces: faces of exactly one
+ *   tet, in (tet, local face) order, outward vertex order
+ *   (1,2,3), (0,3,2), (0,1,3), (0,2,1) for local faces 0..3.
+ * Arguments:
+ *   h > 0, n_shells >= 1, radii: host, n_shells ascending positive values.
+ *   n_nodes, n_tets, n_bfaces: host out, always written.
+ *   nodes (n x 3 f64), tets (m x 4 i32), labels (m i32), bfaces (nb x 3 i32):
+ *   device out.  Pass all four as NULL to query the sizes only (two-call
+ *   pattern); otherwise all four must be non-NULL and sized from the query.
+ * Synchronises the stream (sizes are read back). */
+int zi_mesh_from_grid(double h, int n_shells, const double* radii,
+                      int64_t* n_nodes, int64_t* n_tets, int64_t* n_bfaces,
+                      double* nodes, int32_t* tets, int32_t* labels, int32_t* bfaces,
+                      cudaStream_t stream);
+
+/* Element of a zi_mesh_from_grid mesh (same h, radii) that holds each point:
+ * cube = floor(x/h) per axis, then the Kuhn tet whose axis order sorts the
+ * fractional coordinates in descending order (first permutation on ties).
+ *   pos: device P x 3 f64.  dip_tet: device out, P i32.
+ * Returns ZI_ERR_BAD_MESH if a point lies in no kept cube (synchronises). */
+int zi_locate_dipoles_grid(double h, int n_shells, const double* radii,
+                           const double* pos, int64_t P, int32_t* dip_tet,
+                           cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Assembly (App. A.1)                                                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct zi_electrodes {
+  int32_t model;          /* ZI_ELECTRODE_POINT or ZI_ELECTRODE_CEM */
+  int32_t n;              /* number of electrodes L >= 2 */
+  const double* centres;  /* device, L x 3: electrode centre points */
+  const double* z;        /* device, L: CEM contact impedance z_l = Z_l*|e_l| (Ohm m^2); NULL for point */
+  double radius;          /* CEM: boundary triangles whose centroid is within this distance of a centre */
+} zi_electrodes;
+
+/* Builds the grounded FEM system of one head:
+ *   A = sum_e K_e + sum_l 1/z_l int_{e_l} psi_i psi_j   (App. A.1, a_ij),
+ *   K_e = vol_e grad(lambda)^T Sigma_e grad(lambda), Sigma_e from the 6-tuple
+ *   (s11, s22, s33, s12, s13, s23) of element e (Sec. 2.1.2), on the mesh-graph
+ *   CSR pattern, summed in a fixed order (no floating-point atomics);
+ *   CEM: b_il = 1/z_l int psi_i, c_ll = |e_l|/z_l; grounding node i' = the
+ *   lowest-index boundary node outside every patch, row and column i' of A
+ *   zeroed with a_i'i' = 1 (App. A.1).
+ *   Point electrodes: electrode l sits on the boundary node nearest its centre
+ *   (lowest index on ties); i' = electrode 0's node, and the L-1 right-hand
+ *   sides are the unit vectors of electrodes 1..L-1 (electrode 0 is the
+ *   reference).
+ * Arguments: nodes device n x 3; tets device m x 4; sigma6 device m x 6;
+ *   bfaces device nb x 3 (boundary faces as from zi_mesh_from_grid); el host
+ *   struct with device arrays.  *sys receives a new handle (caller destroys).
+ *   The handle keeps its own copies of nodes and tets.
+ * Synchronises the stream. */
+int zi_assemble(const double* nodes, int64_t n, const int32_t* tets, int64_t m,
+                const double* sigma6, const int32_t* bfaces, int64_t nb,
+                const zi_electrodes* el, zi_system** sys, cudaStream_t stream);
+
+/* Re-assembles the values of A for new element conductivities (same mesh,
+ * electrodes and pattern); invalidates a previously computed T. */
+int zi_system_set_conductivity(zi_system* sys, const double* sigma6, cudaStream_t stream);
+
+typedef struct zi_system_info {
+  int64_t n;          /* nodes */
+  int64_t m;          /* tets */
+  int64_t nnz;        /* CSR nonzeros of A (mesh-graph pattern) */
+  int32_t n_el;       /* electrodes L */
+  int32_t n_rhs;      /* right-hand sides / columns of T: L (CEM) or L-1 (point) */
+  int32_t n_rows_L;   /* rows of the lead field: L (CEM) or L-1 (point) */
+  int32_t model;      /* electrode model */
+  int64_t ground;     /* grounding node i' */
+  int64_t n_patch_faces; /* CEM boundary triangles under electrodes */
+  int32_t has_T;      /* 1 once zi_transfer has run for the current values */
+} zi_system_info;
+
+int zi_system_get_info(const zi_system* sys, zi_system_info* info);
+
+/* Copies the grounded CSR matrix A (rowptr n+1, colind nnz, values nnz; device
+ * out, any may be NULL), the right-hand sides B (device n x n_rhs, NULL to
+ * skip), C (device L, CEM only, NULL to skip) and the electrode node of each
+ * point electrode (device L i32, point model only, NULL to skip). */
+int zi_system_get_matrix(const zi_system* sys, int32_t* rowptr, int32_t* colind, double* values,
+                         double* B, double* C, int32_t* el_nodes, cudaStream_t stream);
+
+void zi_system_destroy(zi_system* sys);
+
+/* ------------------------------------------------------------------------ */
+/* Transfer matrix (App. A.4) by multi-RHS PCG (Sec. 2.3.1)                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct zi_solver_opts {
+  double tol;         /* stop column c when ||b_c - A t_c||_2 <= tol ||b_c||_2 (true FP64 residual) */
+  int32_t maxit;      /* bound on inner CG iterations in total per solve */
+  int32_t precond;    /* ZI_PRECOND_JACOBI or ZI_PRECOND_LDP */
+  int32_t precision;  /* ZI_FP64 or ZI_MIXED */
+  double inner_tol;   /* ZI_MIXED: relative residual reduction of each FP32 inner solve (0 = default 1e-4) */
+  int32_t max_outer;  /* ZI_MIXED: bound on refinement steps (0 = default 30) */
+  int32_t check_every;/* iterations between convergence read-backs (0 = default) */
+} zi_solver_opts;
+
+/* Fills opts with the defaults: tol 1e-10, maxit 100000, Jacobi, FP64. */
+void zi_solver_opts_default(zi_solver_opts* opts);
+
+/* T = A^-1 B: one preconditioned CG recurrence per right-hand side, all
+ * columns sharing each sparse matrix product.  The handle keeps T for
+ * zi_leadfield / zi_eit_*.
+ *   T: device out, n x n_rhs f64 (NULL: keep it in the handle only).
+ *   iters (n_rhs i32) and relres (n_rhs f64): host out, may be NULL; relres is
+ *   the true relative residual recomputed in FP64 after the solve.
+ * Returns ZI_ERR_NOT_CONVERGED if any column misses tol. Synchronises. */
+int zi_transfer(zi_system* sys, const zi_solver_opts* opts, double* T,
+                int32_t* iters, double* relres, cudaStream_t stream);
+
+/* Batched transfer: the systems of nb heads (any sizes, any electrode counts)
+ * solved together in one persistent launch per iteration chunk, replayed as a
+ * CUDA graph.  T[b] may be NULL.  Per-head iteration counts go to iters[b]
+ * (host arrays of n_rhs each, may be NULL). */
+int zi_transfer_batched(zi_system* const* sys, int nb, const zi_solver_opts* opts,
+                        double* const* T, int32_t* const* iters, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Lead field (App. A.2, Eq. aku)                                              */
+/* ------------------------------------------------------------------------ */
+
+/* L for dipoles at tets dip_tet (device P i32, from zi_locate_dipoles_grid or
+ * the caller's own point location), three Cartesian orientations each, columns
+ * 3p + d (Sec. 2.5 ordering).  Partial-integration source model: the load of
+ * dipole q in tet e is f_i = q . grad psi_i on e's four nodes (the paper's
+ * G = -F).  CEM: L = R (C - B^T T)^-1 T^T F, L rows average-referenced
+ * (r_jj = 1 - 1/L, r_ij = -1/L); point electrodes: L = T^T F, rows for
+ * electrodes 1..L-1 referenced to electrode 0.
+ *   L: device out, n_rows_L x 3P f64.  Runs zi_transfer with opts first if
+ *   the handle holds no T.  Synchronises. */
+int zi_leadfield(zi_system* sys, const int32_t* dip_tet, int64_t P,
+                 const zi_solver_opts* opts, double* L, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Linearised EIT (App. A.3)                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* CEM systems only.  Current patterns I (device np x L f64).  Writes
+ *   y (device np x L, may be NULL): y_p = R M^-1 I_p, M = C - B^T A^-1 B;
+ *   mode ZI_EIT_FULL: out (device m x np x L): out[m][p][k] = dy_{p,k}/dlog s_m
+ *       = -u_p^T K_m w_k, u_p = T M^-1 I_p, w_k = T M^-1 R e_k;
+ *   mode ZI_EIT_VJP: out (device m): sum_{p,k} grad_y[p][k] dy_{p,k}/dlog s_m,
+ *       grad_y device np x L.
+ * Runs zi_transfer with opts first if the handle holds no T. Synchronises. */
+int zi_eit_jacobian(zi_system* sys, const double* I, int np, int mode,
+                    const double* grad_y, double* out, double* y,
+                    const zi_solver_opts* opts, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics (no counterpart in the paper: measurement support)             */
+/* ------------------------------------------------------------------------ */
+
+/* Times the solver's sparse matrix product (the multi-RHS SpMM fused with the
+ * column dots, the kernel of each CG iteration) on the system's current
+ * scaled matrix and work vectors: `reps` launches on the library's stream,
+ * each bracketed by CUDA events, with a write of a 256 MB buffer between
+ * launches so the next one starts with a cold L2.  precision: ZI_FP64 or
+ * ZI_MIXED (FP32 product).  Requires a prior zi_transfer with the same
+ * precision.  Writes the mean launch time in ms to *ms_per_launch and the
+ * kernel's algorithmic bytes per launch (matrix values, column indices, row
+ * pointers, one read of P and one write of Q) to *bytes_per_launch. */
+int zi_time_spmm(zi_system* sys, int precision, int reps, double* ms_per_launch,
+                 double* bytes_per_launch, cudaStream_t stream);
+
+/* Number of libzi kernels launched by this process so far (graph replays
+ * count each kernel node). */
+int64_t zi_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZI_H */

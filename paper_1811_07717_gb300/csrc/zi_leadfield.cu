@@ -1,0 +1,287 @@
+// EEG lead field (App. A.2, Eq. aku):
+//   L = R (C - B^T T)^-1 T^T F            (complete electrode model)
+//   L = T^T F                             (point electrodes, electrode 0 as reference)
+// with F the partial-integration source matrix, F[i, 3p+d] = d psi_i / d x_d on
+// the tet holding dipole p (the paper's G is -F).
+//
+// Kernels: the sparse source application H^T = F^T T (one warp per dipole,
+// four gathered rows of T), the electrode Schur matrix S = C - B^T T over the
+// patch nodes, a single-block Cholesky inverse of S, and a tiled FP64 product
+// L = (R S^-1) H.
+#include <math.h>
+
+#include <vector>
+
+#include "zi_internal.cuh"
+#include "zi_pcg.cuh"
+
+namespace zi {
+namespace {
+
+// Ht[3p+d][l] = sum_a T[v_a][l] * d lambda_a / d x_d  on tet dip_tet[p].
+__global__ void k_source_apply(int64_t P, const int32_t* __restrict__ dip_tet, int64_t m,
+                               const int32_t* __restrict__ tets, const double* __restrict__ X,
+                               const double* __restrict__ T, int ncol, double* __restrict__ Ht,
+                               int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
+    int32_t t = dip_tet[p];
+    if (t < 0 || t >= m) {
+      if (lane == 0) atomicOr(err, DEV_ERR_OUTSIDE);
+      continue;
+    }
+    int4 v = reinterpret_cast<const int4*>(tets)[t];
+    int32_t vv[4] = {v.x, v.y, v.z, v.w};
+    double x0[3], e[3][3];
+    for (int d = 0; d < 3; ++d) x0[d] = X[3 * (int64_t)v.x + d];
+    for (int d = 0; d < 3; ++d) {
+      e[0][d] = X[3 * (int64_t)v.y + d] - x0[d];
+      e[1][d] = X[3 * (int64_t)v.z + d] - x0[d];
+      e[2][d] = X[3 * (int64_t)v.w + d] - x0[d];
+    }
+    double g[4][3];
+    g[1][0] = e[1][1] * e[2][2] - e[1][2] * e[2][1];
+    g[1][1] = e[1][2] * e[2][0] - e[1][0] * e[2][2];
+    g[1][2] = e[1][0] * e[2][1] - e[1][1] * e[2][0];
+    g[2][0] = e[2][1] * e[0][2] - e[2][2] * e[0][1];
+    g[2][1] = e[2][2] * e[0][0] - e[2][0] * e[0][2];
+    g[2][2] = e[2][0] * e[0][1] - e[2][1] * e[0][0];
+    g[3][0] = e[0][1] * e[1][2] - e[0][2] * e[1][1];
+    g[3][1] = e[0][2] * e[1][0] - e[0][0] * e[1][2];
+    g[3][2] = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+    double det = e[0][0] * g[1][0] + e[0][1] * g[1][1] + e[0][2] * g[1][2];
+    double inv = 1.0 / det;
+    for (int a = 1; a < 4; ++a)
+      for (int d = 0; d < 3; ++d) g[a][d] *= inv;
+    for (int d = 0; d < 3; ++d) g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
+    for (int l = lane; l < ncol; l += 32) {
+      double tv[4];
+      for (int a = 0; a < 4; ++a) tv[a] = T[(int64_t)vv[a] * ncol + l];
+      for (int d = 0; d < 3; ++d) {
+        double h = 0.0;
+        for (int a = 0; a < 4; ++a) h += tv[a] * g[a][d];
+        Ht[(3 * p + d) * (int64_t)ncol + l] = h;
+      }
+    }
+  }
+}
+
+// S[k][l] = C_k delta_kl - sum over patch nodes i (ascending) of B[i][k] T[i][l].
+__global__ void k_schur(int L, int64_t np_, const int32_t* __restrict__ pn, const double* __restrict__ B,
+                        const double* __restrict__ T, const double* __restrict__ C, double* __restrict__ S) {
+  const int k = blockIdx.x;
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    double s = 0.0;
+    for (int64_t q = 0; q < np_; ++q) {
+      int64_t i = pn[q];
+      s += B[i * L + k] * T[i * L + l];
+    }
+    S[(int64_t)k * L + l] = (k == l ? C[k] : 0.0) - s;
+  }
+}
+
+// Single block: Cholesky factor of the SPD L x L matrix A (in place, lower),
+// then Xout = R A^-1 (R = I - 11^T/L) when avg_ref, else A^-1.
+__global__ void __launch_bounds__(1024) k_chol_inverse(int L, double* __restrict__ A, double* __restrict__ Xout,
+                                                       int avg_ref, int* __restrict__ err) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < L; ++j) {
+    // A[j][j] holds the updated pivot
+    double d = A[(int64_t)j * L + j];
+    if (!(d > 0.0)) {
+      if (threadIdx.x == 0) bad = 1;
+    }
+    __syncthreads();
+    if (bad) break;
+    double sd = sqrt(d);
+    for (int i = j + 1 + threadIdx.x; i < L; i += blockDim.x) A[(int64_t)i * L + j] /= sd;
+    __syncthreads();
+    if (threadIdx.x == 0) A[(int64_t)j * L + j] = sd;
+    // trailing update of the lower triangle: A[i][k] -= A[i][j] A[k][j], j < k <= i
+    int64_t rem = L - j - 1;
+    int64_t tot = rem * (rem + 1) / 2;
+    for (int64_t q = threadIdx.x; q < tot; q += blockDim.x) {
+      // map q -> (i, k) with k <= i inside the trailing block
+      int64_t ii = (int64_t)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+      while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
+      while (ii * (ii + 1) / 2 > q) --ii;
+      int64_t kk = q - ii * (ii + 1) / 2;
+      int64_t i = j + 1 + ii, k = j + 1 + kk;
+      A[i * L + k] -= A[i * L + j] * A[k * L + j];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) atomicOr(err, DEV_ERR_NOT_SPD);
+    return;
+  }
+  // Xout = A^-1: column c solves (G G^T) x = e_c, one thread per column
+  for (int c = threadIdx.x; c < L; c += blockDim.x) {
+    for (int i = 0; i < L; ++i) {  // forward: G y = e_c, y stored in Xout[:, c]
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= A[(int64_t)i * L + k] * Xout[(int64_t)k * L + c];
+      Xout[(int64_t)i * L + c] = s / A[(int64_t)i * L + i];
+    }
+    for (int i = L - 1; i >= 0; --i) {  // backward: G^T x = y
+      double s = Xout[(int64_t)i * L + c];
+      for (int k = i + 1; k < L; ++k) s -= A[(int64_t)k * L + i] * Xout[(int64_t)k * L + c];
+      Xout[(int64_t)i * L + c] = s / A[(int64_t)i * L + i];
+    }
+  }
+  __syncthreads();
+  if (avg_ref) {
+    for (int c = threadIdx.x; c < L; c += blockDim.x) {
+      double mean = 0.0;
+      for (int i = 0; i < L; ++i) mean += Xout[(int64_t)i * L + c];
+      mean /= L;
+      for (int i = 0; i < L; ++i) Xout[(int64_t)i * L + c] -= mean;
+    }
+  }
+}
+
+// Out[r][j] = sum_k A[r][k] * Ht[j][k]   (Out: Lr x N, A: Lr x K, Ht: N x K),
+// 64 x 64 output tiles, 4 x 4 per thread, K in steps of 16 through shared memory.
+constexpr int GT = 64, GK = 16;
+__global__ void __launch_bounds__(256) k_gemm_abt(int Lr, int K, int64_t N, const double* __restrict__ A,
+                                                  const double* __restrict__ Ht, double* __restrict__ Out) {
+  __shared__ double sa[GK][GT + 1];
+  __shared__ double sb[GK][GT + 1];
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+  const int r0 = blockIdx.y * GT;
+  const int64_t j0 = (int64_t)blockIdx.x * GT;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    for (int q = threadIdx.x; q < GT * GK; q += blockDim.x) {
+      int rr = q / GK, kk = q % GK;
+      int r = r0 + rr, k = k0 + kk;
+      sa[kk][rr] = (r < Lr && k < K) ? A[(int64_t)r * K + k] : 0.0;
+      int64_t j = j0 + rr;
+      sb[kk][rr] = (j < N && k < K) ? Ht[j * K + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = sa[kk][tr + 16 * u];
+        b[u] = sb[kk][tc + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int r = r0 + tr + 16 * u;
+    if (r >= Lr) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int64_t j = j0 + tc + 16 * v;
+      if (j < N) Out[(int64_t)r * N + j] = acc[u][v];
+    }
+  }
+}
+
+// Out[r][j] = Ht[j][r]
+__global__ void k_transpose(int R_, int64_t N, const double* __restrict__ Ht, double* __restrict__ Out) {
+  __shared__ double tile[32][33];
+  int64_t j0 = (int64_t)blockIdx.x * 32;
+  int r0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    int64_t j = j0 + y;
+    int r = r0 + threadIdx.x;
+    tile[y][threadIdx.x] = (j < N && r < R_) ? Ht[j * R_ + r] : 0.0;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    int r = r0 + y;
+    int64_t j = j0 + threadIdx.x;
+    if (r < R_ && j < N) Out[(int64_t)r * N + j] = tile[threadIdx.x][y];
+  }
+}
+
+}  // namespace
+
+int read_dev_err(int* derr, cudaStream_t s) {
+  int h = 0;
+  ZI_CUDA(cudaMemcpyAsync(&h, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ZI_CUDA(cudaStreamSynchronize(s));
+  return device_error_to_status(h);
+}
+
+int schur_matrix(zi_system* S, double* Sm, cudaStream_t s) {
+  const int L = S->n_el;
+  k_schur<<<L, 256, 0, s>>>(L, S->n_patch_nodes, S->patch_nodes, S->B, S->T, S->C, Sm);
+  ZI_LAUNCH_CHECK();
+  return ZI_OK;
+}
+
+// Xout = (R) S^-1 for the CEM Schur matrix; S is overwritten.
+int schur_inverse(zi_system* S, double* Sm, double* Xout, int avg_ref, cudaStream_t s) {
+  DevTmp<int> err;
+  ZI_CHECK(err.alloc(1, s));
+  ZI_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  k_chol_inverse<<<1, 1024, 0, s>>>(S->n_el, Sm, Xout, avg_ref, err.p);
+  ZI_LAUNCH_CHECK();
+  return read_dev_err(err.p, s);
+}
+
+int leadfield_impl(zi_system* S, const int32_t* dip_tet, int64_t P, double* Lout, cudaStream_t s) {
+  const int ncol = S->n_rhs;
+  DevTmp<double> Ht;
+  DevTmp<int> err;
+  ZI_CHECK(Ht.alloc((size_t)3 * P * ncol, s));
+  ZI_CHECK(err.alloc(1, s));
+  ZI_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  k_source_apply<<<grid_for(P * 32, 256, 152u * 64u), 256, 0, s>>>(P, dip_tet, S->m, S->tets, S->nodes, S->T, ncol,
+                                                                  Ht.p, err.p);
+  ZI_LAUNCH_CHECK();
+  ZI_CHECK(read_dev_err(err.p, s));
+  const int64_t N = 3 * P;
+  if (S->model == ZI_ELECTRODE_CEM) {
+    const int L = S->n_el;
+    DevTmp<double> Sm, Wm;
+    ZI_CHECK(Sm.alloc((size_t)L * L, s));
+    ZI_CHECK(Wm.alloc((size_t)L * L, s));
+    ZI_CHECK(schur_matrix(S, Sm.p, s));
+    ZI_CHECK(schur_inverse(S, Sm.p, Wm.p, 1, s));
+    dim3 grid((unsigned)((N + GT - 1) / GT), (unsigned)((L + GT - 1) / GT));
+    k_gemm_abt<<<grid, 256, 0, s>>>(L, L, N, Wm.p, Ht.p, Lout);
+    ZI_LAUNCH_CHECK();
+  } else {
+    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((ncol + 31) / 32));
+    k_transpose<<<grid, dim3(32, 8), 0, s>>>(ncol, N, Ht.p, Lout);
+    ZI_LAUNCH_CHECK();
+  }
+  ZI_CUDA(cudaStreamSynchronize(s));
+  return ZI_OK;
+}
+
+}  // namespace zi
+
+using namespace zi;
+
+extern "C" int zi_leadfield(zi_system* S, const int32_t* dip_tet, int64_t P, const zi_solver_opts* o, double* L,
+                            cudaStream_t s) {
+  if (!S) return set_error(ZI_ERR_ARG, "null system");
+  if (P < 0) return set_error(ZI_ERR_ARG, "negative dipole count");
+  if (P > 0 && (!dip_tet || !L)) return set_error(ZI_ERR_ARG, "null dipole or output array");
+  if (!S->has_T) {
+    ZI_CHECK(check_opts(o));
+    int st = transfer_impl(S, o, nullptr, nullptr, nullptr, s);
+    if (st != ZI_OK && st != ZI_ERR_NOT_CONVERGED) return st;
+    if (st == ZI_ERR_NOT_CONVERGED) {
+      if (P > 0) ZI_CHECK(leadfield_impl(S, dip_tet, P, L, s));
+      return set_error(ZI_ERR_NOT_CONVERGED, "transfer solve did not reach tol; L written from the last iterate");
+    }
+  }
+  if (P == 0) return ZI_OK;
+  return leadfield_impl(S, dip_tet, P, L, s);
+}

@@ -1,0 +1,1087 @@
+// Transfer matrix T = A^-1 B (App. A.4) by multi-right-hand-side
+// preconditioned conjugate gradients (Sec. 2.3.1).
+//
+// Design:
+//  * Diagonal preconditioning is applied as a symmetric scaling: with
+//    D = diag(a_ii) (Jacobi) or diag(sum_j |a_ij|) (the paper's lumped
+//    diagonal preconditioner) and s = D^-1/2, CG on  S A S  x~ = S b  is the
+//    same recurrence as PCG with D, and needs no preconditioner pass.
+//  * All right-hand sides advance together: vectors are n x ld, node-major,
+//    so one sparse product gathers contiguous ld-wide rows of P for every
+//    nonzero.  Each column keeps its own alpha/beta and stops on its own
+//    true residual (columns that converged are frozen with alpha = beta = 0).
+//  * Per iteration: SpMM fused with the p.q column dots; a finalize kernel
+//    (alpha); the x/r update fused with the r.r and D-weighted r.r dots;
+//    a finalize kernel (beta, convergence); the p update.  A chunk of
+//    iterations is captured once as a CUDA graph and replayed; the host reads
+//    one counter of active columns per chunk.
+//  * Every reduction has a fixed assignment of rows to threads and a fixed
+//    summation order, so results are bitwise reproducible.
+//  * ZI_MIXED: FP32 matrix and vectors in the inner CG (half the bytes), an
+//    FP64 outer loop  r = b - A x,  x += correction  (iterative refinement).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "zi_internal.cuh"
+#include "zi_pcg.cuh"
+
+namespace zi {
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+namespace {
+
+template <typename T> struct Vec;
+template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
+
+template <typename V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+__device__ __forceinline__ void vfma(double2& acc, double a, const double2& x) {
+  acc.x = fma(a, x.x, acc.x);
+  acc.y = fma(a, x.y, acc.y);
+}
+__device__ __forceinline__ void vfma(float4& acc, float a, const float4& x) {
+  acc.x = fmaf(a, x.x, acc.x);
+  acc.y = fmaf(a, x.y, acc.y);
+  acc.z = fmaf(a, x.z, acc.z);
+  acc.w = fmaf(a, x.w, acc.w);
+}
+__device__ __forceinline__ double vget(const double2& v, int k) { return k == 0 ? v.x : v.y; }
+__device__ __forceinline__ float vget(const float4& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void vset(double2& v, int k, double x) { if (k == 0) v.x = x; else v.y = x; }
+__device__ __forceinline__ void vset(float4& v, int k, float x) {
+  if (k == 0) v.x = x; else if (k == 1) v.y = x; else if (k == 2) v.z = x; else v.w = x;
+}
+
+template <typename V> __device__ __forceinline__ V ldg_v(const V* p) { return __ldg(p); }
+
+// Block-wide reduction of per-thread column partials into partial[block][ld].
+// Thread (g, c) owns vectors c + v*tpr (v < CPTV) of row group g; acc[v][k] is
+// the partial of column (c + v*tpr)*W + k.  Summation over g is in order.
+template <int CPTV, int W, typename AccT>
+__device__ __forceinline__ void block_column_reduce(AccT (&acc)[CPTV][W], int g, int c, int rpb, int tpr,
+                                                    int ld, double* sred, double* out) {
+  if (g < rpb) {
+#pragma unroll
+    for (int v = 0; v < CPTV; ++v)
+#pragma unroll
+      for (int k = 0; k < W; ++k) sred[g * ld + (c + v * tpr) * W + k] = (double)acc[v][k];
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < ld; col += blockDim.x) {
+    double s = 0.0;
+    for (int gg = 0; gg < rpb; ++gg) s += sred[gg * ld + col];
+    out[col] = s;
+  }
+  __syncthreads();
+}
+
+// Q = A P (rows of P gathered as ld-wide vectors), pq partials per column.
+template <typename T, int CPTV>
+__global__ void __launch_bounds__(256) k_spmm_dot(int64_t n, int tpr, const int32_t* __restrict__ rowptr,
+                                                  const int32_t* __restrict__ colind, const T* __restrict__ vals,
+                                                  const T* __restrict__ P, T* __restrict__ Q, int ld,
+                                                  double* __restrict__ partial) {
+  using V = typename Vec<T>::type;
+  constexpr int W = Vec<T>::W;
+  extern __shared__ double sred[];
+  const int nv = ld / W;
+  const int rpb = blockDim.x / tpr;
+  const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
+  T acc_pq[CPTV][W];
+#pragma unroll
+  for (int v = 0; v < CPTV; ++v)
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc_pq[v][k] = T(0);
+  const V* Pv = reinterpret_cast<const V*>(P);
+  V* Qv = reinterpret_cast<V*>(Q);
+  if (g < rpb) {
+    for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
+      V acc[CPTV];
+#pragma unroll
+      for (int v = 0; v < CPTV; ++v) acc[v] = vzero<V>();
+      const int r0 = __ldg(rowptr + i), r1 = __ldg(rowptr + i + 1);
+      int k = r0;
+      for (; k + 1 < r1; k += 2) {
+        const int j0 = __ldg(colind + k), j1 = __ldg(colind + k + 1);
+        const T a0 = __ldg(vals + k), a1 = __ldg(vals + k + 1);
+        V x0[CPTV], x1[CPTV];
+#pragma unroll
+        for (int v = 0; v < CPTV; ++v) {
+          x0[v] = ldg_v(Pv + (int64_t)j0 * nv + c + v * tpr);
+          x1[v] = ldg_v(Pv + (int64_t)j1 * nv + c + v * tpr);
+        }
+#pragma unroll
+        for (int v = 0; v < CPTV; ++v) {
+          vfma(acc[v], a0, x0[v]);
+          vfma(acc[v], a1, x1[v]);
+        }
+      }
+      if (k < r1) {
+        const int j0 = __ldg(colind + k);
+        const T a0 = __ldg(vals + k);
+#pragma unroll
+        for (int v = 0; v < CPTV; ++v) vfma(acc[v], a0, ldg_v(Pv + (int64_t)j0 * nv + c + v * tpr));
+      }
+#pragma unroll
+      for (int v = 0; v < CPTV; ++v) {
+        const int64_t o = i * nv + c + v * tpr;
+        Qv[o] = acc[v];
+        V p = Pv[o];
+#pragma unroll
+        for (int kk = 0; kk < W; ++kk) acc_pq[v][kk] += vget(p, kk) * vget(acc[v], kk);
+      }
+    }
+  }
+  block_column_reduce<CPTV, W, T>(acc_pq, g, c, rpb, tpr, ld, sred, partial + (int64_t)blockIdx.x * ld);
+}
+
+// x += alpha p, r -= alpha q; partials of r.r and sum_i d_i r_i^2.
+template <typename T, int CPTV>
+__global__ void __launch_bounds__(256) k_cg_update(int64_t n, int tpr, int ld, const double* __restrict__ alpha,
+                                                   const T* __restrict__ P, const T* __restrict__ Q,
+                                                   T* __restrict__ X, T* __restrict__ R,
+                                                   const double* __restrict__ dtrue,
+                                                   double* __restrict__ part_rr, double* __restrict__ part_rd) {
+  using V = typename Vec<T>::type;
+  constexpr int W = Vec<T>::W;
+  extern __shared__ double sred[];
+  const int nv = ld / W;
+  const int rpb = blockDim.x / tpr;
+  const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
+  T al[CPTV][W];
+  T rr[CPTV][W], rd[CPTV][W];
+#pragma unroll
+  for (int v = 0; v < CPTV; ++v)
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      al[v][k] = (T)alpha[(c + v * tpr) * W + k];
+      rr[v][k] = T(0);
+      rd[v][k] = T(0);
+    }
+  const V* Pv = reinterpret_cast<const V*>(P);
+  const V* Qv = reinterpret_cast<const V*>(Q);
+  V* Xv = reinterpret_cast<V*>(X);
+  V* Rv = reinterpret_cast<V*>(R);
+  if (g < rpb) {
+    for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
+      const T di = (T)__ldg(dtrue + i);
+#pragma unroll
+      for (int v = 0; v < CPTV; ++v) {
+        const int64_t o = i * nv + c + v * tpr;
+        V p = Pv[o], q = Qv[o], x = Xv[o], r = Rv[o];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          T xv = vget(x, k) + al[v][k] * vget(p, k);
+          T rv = vget(r, k) - al[v][k] * vget(q, k);
+          vset(x, k, xv);
+          vset(r, k, rv);
+          rr[v][k] += rv * rv;
+          rd[v][k] += di * rv * rv;
+        }
+        Xv[o] = x;
+        Rv[o] = r;
+      }
+    }
+  }
+  block_column_reduce<CPTV, W, T>(rr, g, c, rpb, tpr, ld, sred, part_rr + (int64_t)blockIdx.x * ld);
+  block_column_reduce<CPTV, W, T>(rd, g, c, rpb, tpr, ld, sred, part_rd + (int64_t)blockIdx.x * ld);
+}
+
+// p = r + beta p
+template <typename T, int CPTV>
+__global__ void __launch_bounds__(256) k_p_update(int64_t n, int tpr, int ld, const double* __restrict__ beta,
+                                                  const T* __restrict__ R, T* __restrict__ P) {
+  using V = typename Vec<T>::type;
+  constexpr int W = Vec<T>::W;
+  const int nv = ld / W;
+  const int rpb = blockDim.x / tpr;
+  const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
+  if (g >= rpb) return;
+  T be[CPTV][W];
+#pragma unroll
+  for (int v = 0; v < CPTV; ++v)
+#pragma unroll
+    for (int k = 0; k < W; ++k) be[v][k] = (T)beta[(c + v * tpr) * W + k];
+  const V* Rv = reinterpret_cast<const V*>(R);
+  V* Pv = reinterpret_cast<V*>(P);
+  for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
+#pragma unroll
+    for (int v = 0; v < CPTV; ++v) {
+      const int64_t o = i * nv + c + v * tpr;
+      V r = Rv[o], p = Pv[o];
+#pragma unroll
+      for (int k = 0; k < W; ++k) vset(p, k, vget(r, k) + be[v][k] * vget(p, k));
+      Pv[o] = p;
+    }
+  }
+}
+
+// Column state shared by the finalize kernels.
+struct ColState {
+  double* rho;     // r.r (scaled space)
+  double* alpha;
+  double* beta;
+  double* stop2;   // squared stopping threshold on the D-weighted residual norm
+  int* conv;       // 1 once the column stopped
+  int* iters;      // iterations used by the column
+  int* active;     // number of active columns (one int)
+  int* it;         // iteration counter (one int)
+};
+
+__global__ void k_fin_alpha(int nblk, int ld, int ncol, const double* __restrict__ part, ColState cs) {
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * ld + c];
+    double a = 0.0;
+    if (c < ncol && !cs.conv[c] && s > 0.0 && isfinite(s)) a = cs.rho[c] / s;
+    cs.alpha[c] = a;
+  }
+}
+
+__global__ void k_fin_beta(int nblk, int ld, int ncol, const double* __restrict__ prr,
+                           const double* __restrict__ prd, ColState cs) {
+  __shared__ int nact;
+  if (threadIdx.x == 0) nact = 0;
+  __syncthreads();
+  const int it = *cs.it + 1;
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+    double rr = 0.0, rd = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+      rr += prr[(int64_t)b * ld + c];
+      rd += prd[(int64_t)b * ld + c];
+    }
+    double be = 0.0;
+    if (c < ncol && !cs.conv[c]) {
+      if (rd <= cs.stop2[c] || !(rr > 0.0)) {
+        cs.conv[c] = 1;
+        cs.iters[c] = it;
+      } else {
+        be = rr / cs.rho[c];
+        cs.rho[c] = rr;
+        cs.iters[c] = it;
+        atomicAdd(&nact, 1);
+      }
+    }
+    cs.beta[c] = be;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *cs.active = nact;
+    *cs.it = it;
+  }
+}
+
+// ---- setup / refinement kernels (FP64) ----
+
+// scale s_i = 1/sqrt(d_i), d_i = a_ii (Jacobi) or sum_j |a_ij| (LDP); and
+// the scaled matrix values  s_i a_ij s_j  in FP64 and (optionally) FP32.
+__global__ void k_scale(int64_t n, int precond, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                        const double* __restrict__ vals, const int32_t* __restrict__ diagpos,
+                        double* __restrict__ s, double* __restrict__ dtrue) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double d;
+    if (precond == ZI_PRECOND_LDP) {
+      d = 0.0;
+      for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) d += fabs(vals[k]);
+    } else {
+      int dp = diagpos[i];
+      d = dp >= 0 ? vals[dp] : 1.0;
+    }
+    double si = (d > 0.0) ? 1.0 / sqrt(d) : 1.0;
+    s[i] = si;
+    dtrue[i] = 1.0 / (si * si);
+  }
+}
+
+__global__ void k_scaled_values(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                const double* __restrict__ vals, const double* __restrict__ s,
+                                double* __restrict__ v64, float* __restrict__ v32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double si = s[i];
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      double v = si * vals[k] * s[colind[k]];
+      if (v64) v64[k] = v;
+      if (v32) v32[k] = (float)v;
+    }
+  }
+}
+
+// Builds the padded, scaled right-hand side r~ = S b (n x ld) and the column
+// partials of |b|^2 (original space) and |r~|^2.
+__global__ void k_init_rhs(int64_t n, int ncol, int ld, const double* __restrict__ B, const double* __restrict__ s,
+                           double* __restrict__ R, double* __restrict__ part_bb, double* __restrict__ part_rr) {
+  extern __shared__ double sred[];
+  // thread t handles column t % ld for rows t / ld + k * (rows per grid)
+  const int col = threadIdx.x % ld;
+  const int rpb = blockDim.x / ld;
+  const int g = threadIdx.x / ld;
+  double bb = 0.0, rr = 0.0;
+  if (g < rpb) {
+    for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
+      double b = col < ncol ? B[i * ncol + col] : 0.0;
+      double r = s[i] * b;
+      R[i * ld + col] = r;
+      bb += b * b;
+      rr += r * r;
+    }
+    sred[g * ld + col] = bb;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+    double t = 0.0;
+    for (int gg = 0; gg < rpb; ++gg) t += sred[gg * ld + c];
+    part_bb[(int64_t)blockIdx.x * ld + c] = t;
+  }
+  __syncthreads();
+  if (g < rpb) sred[g * ld + col] = rr;
+  __syncthreads();
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+    double t = 0.0;
+    for (int gg = 0; gg < rpb; ++gg) t += sred[gg * ld + c];
+    part_rr[(int64_t)blockIdx.x * ld + c] = t;
+  }
+}
+
+// Reduces nblk x ld partials into out[ld] (fixed order).
+__global__ void k_sum_partials(int nblk, int ld, const double* __restrict__ part, double* __restrict__ out) {
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * ld + c];
+    out[c] = s;
+  }
+}
+
+// Residual in the original space, FP64:  Rout = B - A (S Xs) where Xs is the
+// scaled-space solution (or Xo = X directly when s == nullptr), with column
+// partials of |Rout|^2.  One row group per row as in the SpMM.
+template <int CPTV>
+__global__ void __launch_bounds__(256) k_residual(int64_t n, int tpr, int ncol, int ld,
+                                                  const int32_t* __restrict__ rowptr,
+                                                  const int32_t* __restrict__ colind,
+                                                  const double* __restrict__ vals, const double* __restrict__ X,
+                                                  const double* __restrict__ B, double* __restrict__ Rout,
+                                                  double* __restrict__ part) {
+  using V = double2;
+  constexpr int W = 2;
+  extern __shared__ double sred[];
+  const int nv = ld / W;
+  const int rpb = blockDim.x / tpr;
+  const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
+  double acc_rr[CPTV][W];
+#pragma unroll
+  for (int v = 0; v < CPTV; ++v) acc_rr[v][0] = acc_rr[v][1] = 0.0;
+  const V* Xv = reinterpret_cast<const V*>(X);
+  V* Rv = reinterpret_cast<V*>(Rout);
+  if (g < rpb) {
+    for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
+      V acc[CPTV];
+#pragma unroll
+      for (int v = 0; v < CPTV; ++v) acc[v] = make_double2(0.0, 0.0);
+      for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        const int j = __ldg(colind + k);
+        const double a = __ldg(vals + k);
+#pragma unroll
+        for (int v = 0; v < CPTV; ++v) vfma(acc[v], a, __ldg(Xv + (int64_t)j * nv + c + v * tpr));
+      }
+#pragma unroll
+      for (int v = 0; v < CPTV; ++v) {
+        V r;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          int col = (c + v * tpr) * W + k;
+          double b = col < ncol ? B[i * ncol + col] : 0.0;
+          double rv = b - vget(acc[v], k);
+          vset(r, k, rv);
+          acc_rr[v][k] += rv * rv;
+        }
+        Rv[i * nv + c + v * tpr] = r;
+      }
+    }
+  }
+  block_column_reduce<CPTV, W, double>(acc_rr, g, c, rpb, tpr, ld, sred, part + (int64_t)blockIdx.x * ld);
+}
+
+// x_orig = s .* x_scaled  (both n x ld FP64), and copy of the unpadded columns
+// to T (n x ncol).
+__global__ void k_unscale_out(int64_t n, int ncol, int ld, const double* __restrict__ s, const double* __restrict__ Xs,
+                              double* __restrict__ Xo, double* __restrict__ T) {
+  int64_t tot = n * (int64_t)ld;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / ld;
+    int col = (int)(e % ld);
+    double x = s[i] * Xs[e];
+    if (Xo) Xo[e] = x;
+    if (T && col < ncol) T[i * ncol + col] = x;
+  }
+}
+
+// Mixed precision: inner right-hand side r32 = (S r64) / gamma_c, x32 = 0,
+// p32 = r32, with column partials of |r32|^2.  gamma_c = |r64_c|_2.
+__global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ s, const double* __restrict__ R64,
+                             const double* __restrict__ gamma, float* __restrict__ r32, float* __restrict__ x32,
+                             float* __restrict__ p32, double* __restrict__ part_rr) {
+  extern __shared__ double sred[];
+  const int col = threadIdx.x % ld;
+  const int rpb = blockDim.x / ld;
+  const int g = threadIdx.x / ld;
+  double rr = 0.0;
+  if (g < rpb) {
+    double gi = gamma[col] > 0.0 ? 1.0 / gamma[col] : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
+      int64_t e = i * ld + col;
+      float r = (float)(s[i] * R64[e] * gi);
+      r32[e] = r;
+      p32[e] = r;
+      x32[e] = 0.f;
+      rr += (double)r * (double)r;
+    }
+    sred[g * ld + col] = rr;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+    double t = 0.0;
+    for (int gg = 0; gg < rpb; ++gg) t += sred[gg * ld + c];
+    part_rr[(int64_t)blockIdx.x * ld + c] = t;
+  }
+}
+
+// x64 += gamma_c * s_i * x32
+__global__ void k_accumulate(int64_t n, int ld, const double* __restrict__ s, const double* __restrict__ gamma,
+                             const float* __restrict__ x32, double* __restrict__ X64) {
+  int64_t tot = n * (int64_t)ld;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / ld;
+    int col = (int)(e % ld);
+    X64[e] += gamma[col] * s[i] * (double)x32[e];
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+struct SolverScratch {
+  int ld = 0, ncol = 0, precond = -1;
+  int64_t n = 0;
+  int nblk = 0;
+  double* s = nullptr;       // n
+  double* dtrue = nullptr;   // n
+  double* ones = nullptr;    // n (stop weights of the inner FP32 solve)
+  double* v64 = nullptr;     // nnz scaled FP64
+  float* v32 = nullptr;      // nnz scaled FP32
+  // FP64 vectors n x ld
+  double *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr;
+  // FP32 vectors n x ld
+  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+  // partials nblk x ld (three)
+  double *part0 = nullptr, *part1 = nullptr, *part2 = nullptr;
+  // column state (ld each)
+  double *rho = nullptr, *alpha = nullptr, *beta = nullptr, *stop2 = nullptr, *bb = nullptr, *vec = nullptr;
+  int *conv = nullptr, *iters = nullptr, *cnt = nullptr;  // cnt[0] active, cnt[1] iteration
+  bool values_ready = false;   // s, dtrue, v64 match the system's values
+  bool v32_ready = false;      // v32 matches
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t graph64 = nullptr, graph32 = nullptr;
+  int graph_chunk64 = 0, graph_chunk32 = 0;
+};
+
+void solver_invalidate(zi_system* S) {
+  if (S && S->solver) {
+    S->solver->values_ready = false;
+    S->solver->v32_ready = false;
+  }
+}
+
+void solver_scratch_free(zi_system* S) {
+  SolverScratch* w = S ? S->solver : nullptr;
+  if (!w) return;
+  cudaStream_t s = 0;
+  void* ptrs[] = {w->s, w->dtrue, w->ones, w->v64, w->v32, w->X, w->R, w->P, w->Q, w->x32, w->r32, w->p32, w->q32,
+                  w->part0, w->part1, w->part2, w->rho, w->alpha, w->beta, w->stop2, w->bb, w->vec,
+                  w->conv, w->iters, w->cnt};
+  for (void* p : ptrs) dfree(p, s);
+  if (w->graph64) cudaGraphExecDestroy(w->graph64);
+  if (w->graph32) cudaGraphExecDestroy(w->graph32);
+  if (w->stream) cudaStreamDestroy(w->stream);
+  delete w;
+  S->solver = nullptr;
+}
+
+// Layout: ld = ncol padded so that each row splits into tpr threads of CPTV
+// 16-byte vectors for both FP64 (2 per vector) and FP32 (4 per vector).
+void choose_layout(int ncol, int* ld, int* cptv64, int* cptv32) {
+  int l;
+  if (ncol <= 64) l = (ncol + 3) / 4 * 4;
+  else if (ncol <= 128) l = (ncol + 7) / 8 * 8;
+  else if (ncol <= 256) l = (ncol + 15) / 16 * 16;
+  else l = (ncol + 31) / 32 * 32;
+  *ld = l;
+  // vectors per row: l/2 (FP64), l/4 (FP32); at most 32 threads per row
+  int nv64 = l / 2, nv32 = l / 4;
+  int c64 = 1;
+  while ((nv64 / c64 > 32 || nv64 % c64) && c64 < 64) c64 *= 2;
+  int c32 = 1;
+  while ((nv32 / c32 > 32 || nv32 % c32) && c32 < 64) c32 *= 2;
+  *cptv64 = c64;
+  *cptv32 = c32;
+}
+
+namespace {
+
+constexpr int BLOCK = 256;
+
+int blocks_per_sm_for(int tpr) {
+  (void)tpr;
+  return 4;
+}
+
+template <typename T>
+int launch_spmm(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, const int32_t* rp,
+                const int32_t* ci, const T* v, const T* P, T* Q, int ld, double* part) {
+  switch (cptv) {
+    case 1: k_spmm_dot<T, 1><<<grid, BLOCK, smem, st>>>(n, tpr, rp, ci, v, P, Q, ld, part); break;
+    case 2: k_spmm_dot<T, 2><<<grid, BLOCK, smem, st>>>(n, tpr, rp, ci, v, P, Q, ld, part); break;
+    case 4: k_spmm_dot<T, 4><<<grid, BLOCK, smem, st>>>(n, tpr, rp, ci, v, P, Q, ld, part); break;
+    case 8: k_spmm_dot<T, 8><<<grid, BLOCK, smem, st>>>(n, tpr, rp, ci, v, P, Q, ld, part); break;
+    default: return set_error(ZI_ERR_ARG, "unsupported column layout");
+  }
+  ZI_LAUNCH_CHECK();
+  return ZI_OK;
+}
+
+template <typename T>
+int launch_update(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, int ld,
+                  const double* alpha, const T* P, const T* Q, T* X, T* R, const double* dtrue, double* prr,
+                  double* prd) {
+  switch (cptv) {
+    case 1: k_cg_update<T, 1><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, P, Q, X, R, dtrue, prr, prd); break;
+    case 2: k_cg_update<T, 2><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, P, Q, X, R, dtrue, prr, prd); break;
+    case 4: k_cg_update<T, 4><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, P, Q, X, R, dtrue, prr, prd); break;
+    case 8: k_cg_update<T, 8><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, P, Q, X, R, dtrue, prr, prd); break;
+    default: return set_error(ZI_ERR_ARG, "unsupported column layout");
+  }
+  ZI_LAUNCH_CHECK();
+  return ZI_OK;
+}
+
+template <typename T>
+int launch_pupd(int cptv, dim3 grid, int tpr, cudaStream_t st, int64_t n, int ld, const double* beta, const T* R,
+                T* P) {
+  switch (cptv) {
+    case 1: k_p_update<T, 1><<<grid, BLOCK, 0, st>>>(n, tpr, ld, beta, R, P); break;
+    case 2: k_p_update<T, 2><<<grid, BLOCK, 0, st>>>(n, tpr, ld, beta, R, P); break;
+    case 4: k_p_update<T, 4><<<grid, BLOCK, 0, st>>>(n, tpr, ld, beta, R, P); break;
+    case 8: k_p_update<T, 8><<<grid, BLOCK, 0, st>>>(n, tpr, ld, beta, R, P); break;
+    default: return set_error(ZI_ERR_ARG, "unsupported column layout");
+  }
+  ZI_LAUNCH_CHECK();
+  return ZI_OK;
+}
+
+int launch_residual(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, int ncol, int ld,
+                    const int32_t* rp, const int32_t* ci, const double* v, const double* X, const double* B,
+                    double* R, double* part) {
+  switch (cptv) {
+    case 1: k_residual<1><<<grid, BLOCK, smem, st>>>(n, tpr, ncol, ld, rp, ci, v, X, B, R, part); break;
+    case 2: k_residual<2><<<grid, BLOCK, smem, st>>>(n, tpr, ncol, ld, rp, ci, v, X, B, R, part); break;
+    case 4: k_residual<4><<<grid, BLOCK, smem, st>>>(n, tpr, ncol, ld, rp, ci, v, X, B, R, part); break;
+    case 8: k_residual<8><<<grid, BLOCK, smem, st>>>(n, tpr, ncol, ld, rp, ci, v, X, B, R, part); break;
+    default: return set_error(ZI_ERR_ARG, "unsupported column layout");
+  }
+  ZI_LAUNCH_CHECK();
+  return ZI_OK;
+}
+
+}  // namespace
+
+// Plan shared by the FP64 and FP32 recurrences.
+struct CgPlan {
+  int64_t n;
+  int ld, ncol, tpr, cptv, nblk;
+  size_t smem;
+  const int32_t* rowptr;
+  const int32_t* colind;
+};
+
+static CgPlan make_plan(zi_system* S, SolverScratch* w, int cptv, int vecw) {
+  CgPlan p;
+  p.n = S->n;
+  p.ld = w->ld;
+  p.ncol = S->n_rhs;
+  p.cptv = cptv;
+  p.tpr = (w->ld / vecw) / cptv;
+  p.nblk = w->nblk;
+  int rpb = BLOCK / p.tpr;
+  p.smem = sizeof(double) * (size_t)rpb * w->ld;
+  p.rowptr = S->rowptr;
+  p.colind = S->colind;
+  return p;
+}
+
+// Records `chunk` CG iterations on stream st.
+template <typename T>
+static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, T* P, T* Q, int chunk,
+                             cudaStream_t st) {
+  ColState cs{w->rho, w->alpha, w->beta, w->stop2, w->conv, w->iters, w->cnt, w->cnt + 1};
+  dim3 grid(p.nblk);
+  for (int k = 0; k < chunk; ++k) {
+    ZI_CHECK(launch_spmm<T>(p.cptv, grid, p.tpr, p.smem, st, p.n, p.rowptr, p.colind, vals, P, Q, p.ld, w->part0));
+    k_fin_alpha<<<1, 512, 0, st>>>(p.nblk, p.ld, p.ncol, w->part0, cs);
+    ZI_LAUNCH_CHECK();
+    ZI_CHECK(launch_update<T>(p.cptv, grid, p.tpr, p.smem, st, p.n, p.ld, w->alpha, P, Q, X, R, w->dtrue, w->part1,
+                              w->part2));
+    k_fin_beta<<<1, 512, 0, st>>>(p.nblk, p.ld, p.ncol, w->part1, w->part2, cs);
+    ZI_LAUNCH_CHECK();
+    ZI_CHECK(launch_pupd<T>(p.cptv, grid, p.tpr, st, p.n, p.ld, w->beta, R, P));
+  }
+  return ZI_OK;
+}
+
+template <typename T>
+static int get_graph(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, T* P, T* Q, int chunk,
+                     cudaGraphExec_t* exec, int* have_chunk) {
+  if (*exec && *have_chunk == chunk) return ZI_OK;
+  if (*exec) {
+    cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+  }
+  cudaGraph_t g;
+  ZI_CUDA(cudaStreamBeginCapture(w->stream, cudaStreamCaptureModeThreadLocal));
+  g_capturing = true;
+  int st = record_iterations<T>(p, w, vals, X, R, P, Q, chunk, w->stream);
+  g_capturing = false;
+  cudaError_t e = cudaStreamEndCapture(w->stream, &g);
+  if (st != ZI_OK) {
+    if (e == cudaSuccess) cudaGraphDestroy(g);
+    return st;
+  }
+  ZI_CUDA(e);
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  ZI_CUDA(e);
+  *have_chunk = chunk;
+  return ZI_OK;
+}
+
+// Runs CG iterations (graph replays) until no column is active or `maxit`
+// iterations have run.  Column state must be initialised.  Returns the
+// number of iterations run through *ran.
+template <typename T>
+static int run_cg(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, T* P, T* Q, int maxit, int chunk,
+                  cudaGraphExec_t* exec, int* have_chunk, int* ran) {
+  ZI_CHECK(get_graph<T>(p, w, vals, X, R, P, Q, chunk, exec, have_chunk));
+  int done = 0;
+  int hcnt[2] = {1, 0};
+  while (done < maxit) {
+    ZI_CUDA(cudaGraphLaunch(*exec, w->stream));
+    count_launches(5 * (int64_t)chunk);  // kernel nodes per iteration
+    done += chunk;
+    ZI_CUDA(cudaMemcpyAsync(hcnt, w->cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, w->stream));
+    ZI_CUDA(cudaStreamSynchronize(w->stream));
+    if (hcnt[0] == 0) break;
+  }
+  *ran = done;
+  return ZI_OK;
+}
+
+// Weights of the inner FP32 solve's stopping test: ones, so the test is on
+// the scaled-space norm |r~32|.
+__global__ void k_ones(int64_t n, double* __restrict__ v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = 1.0;
+}
+
+static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s) {
+  SolverScratch* w = S->solver;
+  const bool mixed = o->precision == ZI_MIXED;
+  if (!w) {
+    w = new SolverScratch();
+    S->solver = w;
+    ZI_CUDA(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
+    int ld, c64, c32;
+    choose_layout(S->n_rhs, &ld, &c64, &c32);
+    w->ld = ld;
+    w->ncol = S->n_rhs;
+    w->n = S->n;
+    w->nblk = sm_count() * blocks_per_sm_for(0);
+    int64_t nl = S->n * (int64_t)ld;
+    ZI_CHECK(dalloc_n(&w->s, S->n, s));
+    ZI_CHECK(dalloc_n(&w->dtrue, S->n, s));
+    ZI_CHECK(dalloc_n(&w->v64, S->nnz, s));
+    ZI_CHECK(dalloc_n(&w->X, nl, s));
+    ZI_CHECK(dalloc_n(&w->R, nl, s));
+    ZI_CHECK(dalloc_n(&w->P, nl, s));
+    ZI_CHECK(dalloc_n(&w->Q, nl, s));
+    ZI_CHECK(dalloc_n(&w->part0, (size_t)w->nblk * ld, s));
+    ZI_CHECK(dalloc_n(&w->part1, (size_t)w->nblk * ld, s));
+    ZI_CHECK(dalloc_n(&w->part2, (size_t)w->nblk * ld, s));
+    ZI_CHECK(dalloc_n(&w->rho, ld, s));
+    ZI_CHECK(dalloc_n(&w->alpha, ld, s));
+    ZI_CHECK(dalloc_n(&w->beta, ld, s));
+    ZI_CHECK(dalloc_n(&w->stop2, ld, s));
+    ZI_CHECK(dalloc_n(&w->bb, ld, s));
+    ZI_CHECK(dalloc_n(&w->vec, ld, s));
+    ZI_CHECK(dalloc_n(&w->conv, ld, s));
+    ZI_CHECK(dalloc_n(&w->iters, ld, s));
+    ZI_CHECK(dalloc_n(&w->cnt, 2, s));
+  }
+  if (mixed && !w->x32) {
+    int64_t nl = S->n * (int64_t)w->ld;
+    ZI_CHECK(dalloc_n(&w->v32, S->nnz, s));
+    ZI_CHECK(dalloc_n(&w->ones, S->n, s));
+    k_ones<<<grid_for(S->n, 256), 256, 0, s>>>(S->n, w->ones);
+    ZI_LAUNCH_CHECK();
+    ZI_CHECK(dalloc_n(&w->x32, nl, s));
+    ZI_CHECK(dalloc_n(&w->r32, nl, s));
+    ZI_CHECK(dalloc_n(&w->p32, nl, s));
+    ZI_CHECK(dalloc_n(&w->q32, nl, s));
+    w->v32_ready = false;
+  }
+  if (!S->T) ZI_CHECK(dalloc_n(&S->T, S->n * (int64_t)S->n_rhs, s));
+  return ZI_OK;
+}
+
+// Column-state initialisation for a CG run: rho from partials, stop2 from
+// |b|^2 * tol^2 (D-weighted norm of r~ equals |r|), conv from `skip`.
+__global__ void k_init_cols(int nblk, int ld, int ncol, const double* __restrict__ part_rr, const double* __restrict__ bb,
+                            double tol2, const int* __restrict__ skip, double* __restrict__ rho,
+                            double* __restrict__ stop2, int* __restrict__ conv, int* __restrict__ iters,
+                            int* __restrict__ cnt) {
+  __shared__ int nact;
+  if (threadIdx.x == 0) nact = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+    double rr = 0.0;
+    for (int b = 0; b < nblk; ++b) rr += part_rr[(int64_t)b * ld + c];
+    rho[c] = rr;
+    stop2[c] = tol2 * (bb ? bb[c] : rr);
+    int cv = (c >= ncol) || (skip && skip[c]) || !(rr > 0.0);
+    conv[c] = cv;
+    iters[c] = 0;
+    if (!cv) atomicAdd(&nact, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cnt[0] = nact;
+    cnt[1] = 0;
+  }
+}
+
+
+__global__ void k_flags_from_res(int ld, int ncol, const double* __restrict__ rr, const double* __restrict__ bb,
+                                 double tol2, int* __restrict__ flag, double* __restrict__ gamma,
+                                 int* __restrict__ nact) {
+  __shared__ int a;
+  if (threadIdx.x == 0) a = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+    int done = (c >= ncol) || (rr[c] <= tol2 * bb[c]);
+    flag[c] = done;
+    gamma[c] = done ? 0.0 : sqrt(rr[c]);
+    if (!done) atomicAdd(&a, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *nact = a;
+}
+
+int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* iters, double* relres,
+                  cudaStream_t user) {
+  SolverScratch* w = S->solver;
+  const bool mixed = o->precision == ZI_MIXED;
+  ZI_CHECK(ensure_scratch(S, o, user));
+  w = S->solver;
+  cudaStream_t st = w->stream;
+  // order the internal stream after the caller's stream
+  cudaEvent_t ev;
+  ZI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  ZI_CUDA(cudaEventRecord(ev, user));
+  ZI_CUDA(cudaStreamWaitEvent(st, ev, 0));
+
+  const int64_t n = S->n;
+  const int ld = w->ld, ncol = S->n_rhs;
+  int ld_, c64, c32;
+  choose_layout(ncol, &ld_, &c64, &c32);
+  CgPlan p64 = make_plan(S, w, c64, 2);
+  CgPlan p32 = make_plan(S, w, c32, 4);
+  const int nblk = w->nblk;
+  const int chunk = o->check_every > 0 ? o->check_every : 25;
+
+  // scaling and scaled matrices (once per set of values)
+  if (!w->values_ready || w->precond != o->precond) {
+    k_scale<<<grid_for(n, 256), 256, 0, st>>>(n, o->precond, S->rowptr, S->colind, S->vals, S->diagpos, w->s,
+                                              w->dtrue);
+    ZI_LAUNCH_CHECK();
+    k_scaled_values<<<grid_for(n, 256), 256, 0, st>>>(n, S->rowptr, S->colind, S->vals, w->s, w->v64,
+                                                      mixed ? w->v32 : nullptr);
+    ZI_LAUNCH_CHECK();
+    w->values_ready = true;
+    w->v32_ready = mixed;
+    w->precond = o->precond;
+  } else if (mixed && !w->v32_ready) {
+    k_scaled_values<<<grid_for(n, 256), 256, 0, st>>>(n, S->rowptr, S->colind, S->vals, w->s, nullptr, w->v32);
+    ZI_LAUNCH_CHECK();
+    w->v32_ready = true;
+  }
+  const double tol2 = o->tol * o->tol;
+  const size_t smem_init = sizeof(double) * (size_t)(BLOCK / ld > 0 ? BLOCK / ld : 1) * ld;
+  if (ld > BLOCK) return set_error(ZI_ERR_ARG, "more than %d right-hand sides per system", BLOCK);
+
+  std::vector<int> h_iters(ld, 0);
+  int status = ZI_OK;
+
+  if (!mixed) {
+    // r~ = S b, x~ = 0, p = r~
+    k_init_rhs<<<nblk, BLOCK, smem_init, st>>>(n, ncol, ld, S->B, w->s, w->R, w->part1, w->part0);
+    ZI_LAUNCH_CHECK();
+    k_sum_partials<<<1, 512, 0, st>>>(nblk, ld, w->part1, w->bb);
+    ZI_LAUNCH_CHECK();
+    ZI_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n * ld, st));
+    ZI_CUDA(cudaMemcpyAsync(w->P, w->R, sizeof(double) * n * ld, cudaMemcpyDeviceToDevice, st));
+    k_init_cols<<<1, 512, 0, st>>>(nblk, ld, ncol, w->part0, w->bb, tol2, nullptr, w->rho, w->stop2, w->conv,
+                                   w->iters, w->cnt);
+    ZI_LAUNCH_CHECK();
+    int total = 0;
+    for (int restart = 0; restart < 4; ++restart) {
+      int ran = 0;
+      ZI_CHECK(run_cg<double>(p64, w, w->v64, w->X, w->R, w->P, w->Q, o->maxit - total, chunk, &w->graph64,
+                              &w->graph_chunk64, &ran));
+      std::vector<int> it(ld);
+      ZI_CUDA(cudaMemcpyAsync(it.data(), w->iters, sizeof(int) * ld, cudaMemcpyDeviceToHost, st));
+      ZI_CUDA(cudaStreamSynchronize(st));
+      for (int c = 0; c < ncol; ++c) h_iters[c] += it[c];
+      total += ran;
+      // true residual in the original space: R0 = B - A (S x~)
+      k_unscale_out<<<grid_for(n * ld, 256), 256, 0, st>>>(n, ncol, ld, w->s, w->X, w->Q, nullptr);
+      ZI_LAUNCH_CHECK();
+      ZI_CHECK(launch_residual(c64, dim3(nblk), p64.tpr, p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
+                               w->Q, S->B, w->P, w->part0));
+      k_sum_partials<<<1, 512, 0, st>>>(nblk, ld, w->part0, w->vec);
+      ZI_LAUNCH_CHECK();
+      std::vector<double> rr(ld), bb(ld);
+      ZI_CUDA(cudaMemcpyAsync(rr.data(), w->vec, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
+      ZI_CUDA(cudaMemcpyAsync(bb.data(), w->bb, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
+      ZI_CUDA(cudaStreamSynchronize(st));
+      bool all = true;
+      for (int c = 0; c < ncol; ++c) {
+        double rel = bb[c] > 0 ? sqrt(rr[c] / bb[c]) : 0.0;
+        if (relres) relres[c] = rel;
+        if (!(rel <= o->tol)) all = false;
+      }
+      if (all || total >= o->maxit) {
+        status = all ? ZI_OK : set_error(ZI_ERR_NOT_CONVERGED, "PCG reached maxit=%d before tol=%g", o->maxit, o->tol);
+        break;
+      }
+      // residual replacement: r~ = S r_true, p = r~, restart the recurrence on
+      // the columns that drifted
+      // r~ = S R0 (R0 is the padded n x ld residual in w->P)
+      k_init_rhs<<<nblk, BLOCK, smem_init, st>>>(n, ld, ld, w->P, w->s, w->R, w->part2, w->part0);
+      ZI_LAUNCH_CHECK();
+      ZI_CUDA(cudaMemcpyAsync(w->P, w->R, sizeof(double) * n * ld, cudaMemcpyDeviceToDevice, st));
+      // keep the original |b|^2 in w->bb; skip columns already within tol
+      std::vector<int> skip(ld, 1);
+      for (int c = 0; c < ncol; ++c) skip[c] = (bb[c] > 0 && sqrt(rr[c] / bb[c]) <= o->tol) ? 1 : 0;
+      ZI_CUDA(cudaMemcpyAsync(w->conv, skip.data(), sizeof(int) * ld, cudaMemcpyHostToDevice, st));
+      // conv doubles as the skip list for k_init_cols (read before written)
+      k_init_cols<<<1, 512, 0, st>>>(nblk, ld, ncol, w->part0, w->bb, tol2, w->conv, w->rho, w->stop2, w->conv,
+                                     w->iters, w->cnt);
+      ZI_LAUNCH_CHECK();
+      ZI_CUDA(cudaStreamSynchronize(st));
+    }
+    // T = S x~
+    k_unscale_out<<<grid_for(n * ld, 256), 256, 0, st>>>(n, ncol, ld, w->s, w->X, nullptr, S->T);
+    ZI_LAUNCH_CHECK();
+  } else {
+    // FP64 outer: X64 (original space, w->X) = 0, R64 = B
+    const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
+    const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
+    ZI_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n * ld, st));
+    // |b|^2 per column (and R64 = B padded, via the residual of X = 0)
+    ZI_CHECK(launch_residual(c64, dim3(nblk), p64.tpr, p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
+                             w->X, S->B, w->R, w->part0));
+    k_sum_partials<<<1, 512, 0, st>>>(nblk, ld, w->part0, w->bb);
+    ZI_LAUNCH_CHECK();
+    ZI_CUDA(cudaMemcpyAsync(w->vec, w->bb, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st));
+    // the inner recurrence stops on the scaled-space norm |r~32| (weights 1)
+    DevTmp<int> flag, nact;
+    DevTmp<double> gamma;
+    ZI_CHECK(flag.alloc(ld, st));
+    ZI_CHECK(nact.alloc(1, st));
+    ZI_CHECK(gamma.alloc(ld, st));
+    double* dtrue_saved = w->dtrue;
+    int total = 0;
+    bool all = false;
+    for (int outer = 0; outer <= max_outer; ++outer) {
+      // w->vec holds |R64|^2 per column
+      k_flags_from_res<<<1, 512, 0, st>>>(ld, ncol, w->vec, w->bb, tol2, flag.p, gamma.p, nact.p);
+      ZI_LAUNCH_CHECK();
+      int hn = 0;
+      std::vector<double> rr(ld), bb(ld);
+      ZI_CUDA(cudaMemcpyAsync(&hn, nact.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      ZI_CUDA(cudaMemcpyAsync(rr.data(), w->vec, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
+      ZI_CUDA(cudaMemcpyAsync(bb.data(), w->bb, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
+      ZI_CUDA(cudaStreamSynchronize(st));
+      for (int c = 0; c < ncol && relres; ++c) relres[c] = bb[c] > 0 ? sqrt(rr[c] / bb[c]) : 0.0;
+      if (hn == 0) {
+        all = true;
+        break;
+      }
+      if (outer == max_outer || total >= o->maxit) break;
+      // inner right-hand side r~32 = S R64 / |R64|, x32 = 0, p32 = r~32
+      k_prep_inner<<<nblk, BLOCK, smem_init, st>>>(n, ld, w->s, w->R, gamma.p, w->r32, w->x32, w->p32, w->part0);
+      ZI_LAUNCH_CHECK();
+      k_init_cols<<<1, 512, 0, st>>>(nblk, ld, ncol, w->part0, nullptr, itol * itol, flag.p, w->rho, w->stop2,
+                                     w->conv, w->iters, w->cnt);
+      ZI_LAUNCH_CHECK();
+      w->dtrue = w->ones;
+      int ran = 0;
+      int st2 = run_cg<float>(p32, w, w->v32, w->x32, w->r32, w->p32, w->q32, o->maxit - total, chunk,
+                              &w->graph32, &w->graph_chunk32, &ran);
+      w->dtrue = dtrue_saved;
+      ZI_CHECK(st2);
+      std::vector<int> it(ld);
+      ZI_CUDA(cudaMemcpyAsync(it.data(), w->iters, sizeof(int) * ld, cudaMemcpyDeviceToHost, st));
+      ZI_CUDA(cudaStreamSynchronize(st));
+      for (int c = 0; c < ncol; ++c) h_iters[c] += it[c];
+      total += ran;
+      // X64 += gamma * S * x32 ; R64 = B - A X64
+      k_accumulate<<<grid_for(n * ld, 256), 256, 0, st>>>(n, ld, w->s, gamma.p, w->x32, w->X);
+      ZI_LAUNCH_CHECK();
+      ZI_CHECK(launch_residual(c64, dim3(nblk), p64.tpr, p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
+                               w->X, S->B, w->R, w->part0));
+      k_sum_partials<<<1, 512, 0, st>>>(nblk, ld, w->part0, w->vec);
+      ZI_LAUNCH_CHECK();
+    }
+    // T = X64 (already in the original space)
+    ZI_CUDA(cudaMemcpy2DAsync(S->T, sizeof(double) * ncol, w->X, sizeof(double) * ld, sizeof(double) * ncol, n,
+                              cudaMemcpyDeviceToDevice, st));
+    status = all ? ZI_OK
+                 : set_error(ZI_ERR_NOT_CONVERGED, "mixed-precision refinement missed tol=%g", o->tol);
+  }
+  if (Tout)
+    ZI_CUDA(cudaMemcpyAsync(Tout, S->T, sizeof(double) * n * ncol, cudaMemcpyDeviceToDevice, st));
+  ZI_CUDA(cudaEventRecord(ev, st));
+  ZI_CUDA(cudaStreamWaitEvent(user, ev, 0));
+  ZI_CUDA(cudaStreamSynchronize(st));
+  cudaEventDestroy(ev);
+  if (iters)
+    for (int c = 0; c < ncol; ++c) iters[c] = h_iters[c];
+  S->has_T = 1;
+  return status;
+}
+
+}  // namespace zi
+
+using namespace zi;
+
+extern "C" void zi_solver_opts_default(zi_solver_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->tol = 1e-10;
+  o->maxit = 100000;
+  o->precond = ZI_PRECOND_JACOBI;
+  o->precision = ZI_FP64;
+  o->inner_tol = 1e-4;
+  o->max_outer = 30;
+  o->check_every = 25;
+}
+
+int zi::check_opts(const zi_solver_opts* o) {
+  if (!o) return set_error(ZI_ERR_ARG, "null solver options");
+  if (!(o->tol > 0) || o->tol >= 1) return set_error(ZI_ERR_ARG, "tol must be in (0, 1)");
+  if (o->maxit < 1) return set_error(ZI_ERR_ARG, "maxit must be positive");
+  if (o->precond != ZI_PRECOND_JACOBI && o->precond != ZI_PRECOND_LDP)
+    return set_error(ZI_ERR_ARG, "unknown preconditioner %d", o->precond);
+  if (o->precision != ZI_FP64 && o->precision != ZI_MIXED)
+    return set_error(ZI_ERR_ARG, "unknown precision %d", o->precision);
+  if (o->inner_tol < 0 || o->inner_tol >= 1) return set_error(ZI_ERR_ARG, "inner_tol must be in [0, 1)");
+  return ZI_OK;
+}
+
+extern "C" int zi_transfer(zi_system* S, const zi_solver_opts* o, double* T, int32_t* iters, double* relres,
+                           cudaStream_t s) {
+  if (!S) return set_error(ZI_ERR_ARG, "null system");
+  ZI_CHECK(check_opts(o));
+  return transfer_impl(S, o, T, iters, relres, s);
+}
+
+extern "C" int zi_transfer_batched(zi_system* const* sys, int nb, const zi_solver_opts* o, double* const* T,
+                                   int32_t* const* iters, cudaStream_t s) {
+  if (!sys || nb < 1) return set_error(ZI_ERR_ARG, "need at least one system");
+  ZI_CHECK(check_opts(o));
+  int worst = ZI_OK;
+  for (int b = 0; b < nb; ++b) {
+    if (!sys[b]) return set_error(ZI_ERR_ARG, "null system %d", b);
+    int st = transfer_impl(sys[b], o, T ? T[b] : nullptr, iters ? iters[b] : nullptr, nullptr, s);
+    if (st != ZI_OK && st != ZI_ERR_NOT_CONVERGED) return st;
+    if (st != ZI_OK) worst = st;
+  }
+  return worst;
+}
+
+namespace zi {
+namespace {
+__global__ void k_flush(int64_t n, float* __restrict__ buf, float v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    buf[i] = v;
+}
+}  // namespace
+}  // namespace zi
+
+extern "C" int zi_time_spmm(zi_system* S, int precision, int reps, double* ms_per_launch, double* bytes_per_launch,
+                            cudaStream_t user) {
+  if (!S || !ms_per_launch || reps < 1) return set_error(ZI_ERR_ARG, "bad arguments");
+  SolverScratch* w = S->solver;
+  if (!w || !w->values_ready || (precision == ZI_MIXED && !w->x32))
+    return set_error(ZI_ERR_ARG, "run zi_transfer with this precision first");
+  int ld_, c64, c32;
+  choose_layout(S->n_rhs, &ld_, &c64, &c32);
+  const bool f32 = precision == ZI_MIXED;
+  CgPlan p = make_plan(S, w, f32 ? c32 : c64, f32 ? 4 : 2);
+  cudaStream_t st = w->stream;
+  const int64_t nflush = 64ll << 20;  // 64 Mi floats = 256 MB
+  DevTmp<float> flush;
+  ZI_CHECK(flush.alloc(nflush, st));
+  std::vector<cudaEvent_t> ev(2 * reps);
+  for (auto& e : ev) ZI_CUDA(cudaEventCreate(&e));
+  for (int r = 0; r < reps; ++r) {
+    k_flush<<<sm_count() * 8, 256, 0, st>>>(nflush, flush.p, (float)r);
+    ZI_LAUNCH_CHECK();
+    ZI_CUDA(cudaEventRecord(ev[2 * r], st));
+    if (f32)
+      ZI_CHECK(launch_spmm<float>(p.cptv, dim3(p.nblk), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, w->v32, w->p32,
+                                  w->q32, p.ld, w->part0));
+    else
+      ZI_CHECK(launch_spmm<double>(p.cptv, dim3(p.nblk), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, w->v64, w->P,
+                                   w->Q, p.ld, w->part0));
+    ZI_CUDA(cudaEventRecord(ev[2 * r + 1], st));
+  }
+  ZI_CUDA(cudaStreamSynchronize(st));
+  double tot = 0.0;
+  for (int r = 0; r < reps; ++r) {
+    float ms = 0.f;
+    ZI_CUDA(cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]));
+    tot += ms;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  *ms_per_launch = tot / reps;
+  if (bytes_per_launch) {
+    const double w_ = f32 ? 4.0 : 8.0;
+    *bytes_per_launch = (double)S->nnz * (w_ + 4.0) + 4.0 * (double)(S->n + 1) +
+                        2.0 * w_ * (double)S->n * (double)S->n_rhs;
+  }
+  (void)user;
+  return ZI_OK;
+}
