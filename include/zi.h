@@ -244,6 +244,35 @@ int zi_eit_jacobian(zi_system* sys, const double* I, int np, int mode,
                     const zi_solver_opts* opts, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Lead field without device allocation (no counterpart in the paper)         */
+/* ------------------------------------------------------------------------ */
+
+/* Size of the fixed device scratch used by zi_leadfield_noalloc: 8 MiB, of
+ * which the first 256 bytes hold an error word and the rest doubles. */
+#define ZI_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* The same lead field as zi_leadfield, for callers that cannot allocate
+ * device memory while it runs: applications that hand the whole GPU to their
+ * own allocator up front (a library allocation would fail or fragment it),
+ * and code that must not allocate inside a latency-critical loop.  It calls no
+ * cudaMalloc, cudaFree or allocating routine; its scratch is one fixed array in
+ * the library's device memory (ZI_NOALLOC_SCRATCH_BYTES on every GPU that
+ * loads the library, held until the process exits).
+ *   The system must already hold T (zi_transfer has run; otherwise ZI_ERR_ARG,
+ *   since solving would allocate).  dip_tet: device P i32; L: device out,
+ *   n_rows_L x 3P f64, as in zi_leadfield.
+ *   Scratch need: 3*P*n_rows_L doubles, plus 2*L*L for CEM systems; a call
+ *   needing more than (ZI_NOALLOC_SCRATCH_BYTES - 256) / 8 doubles returns
+ *   ZI_ERR_ARG with the limit in the message.
+ *   The first call on a device looks up the scratch address
+ *   (cudaGetSymbolAddress), so make that first call before any stream capture.
+ *   All calls share the one array: calls that overlap on the GPU (other
+ *   streams, other threads) race and must be serialised by the caller.
+ * Synchronises the stream. */
+int zi_leadfield_noalloc(zi_system* sys, const int32_t* dip_tet, int64_t P, double* L,
+                         cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Diagnostics (no counterpart in the paper: measurement support)             */
 /* ------------------------------------------------------------------------ */
 

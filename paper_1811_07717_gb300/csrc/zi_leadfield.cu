@@ -10,6 +10,7 @@
 // L = (R S^-1) H.
 #include <math.h>
 
+#include <mutex>
 #include <vector>
 
 #include "zi_internal.cuh"
@@ -284,4 +285,95 @@ extern "C" int zi_leadfield(zi_system* S, const int32_t* dip_tet, int64_t P, con
   }
   if (P == 0) return ZI_OK;
   return leadfield_impl(S, dip_tet, P, L, s);
+}
+
+// ---------------------------------------------------------------------------
+// Lead field without device allocation: the same kernels as zi_leadfield, with
+// their scratch (error word, H^T, S, (R) S^-1) in one fixed device array.
+// ---------------------------------------------------------------------------
+
+namespace zi {
+namespace {
+
+constexpr size_t NOALLOC_WORDS = ZI_NOALLOC_SCRATCH_BYTES / sizeof(double);
+constexpr size_t NOALLOC_HEAD = 256 / sizeof(double);  // error word lives here
+
+// In host code this name is only a stand-in for the device array; kernels get
+// the device address looked up below.
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_WORDS];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64];
+
+// Device address of the scratch on the current device, looked up once per
+// device with that device current.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  ZI_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(ZI_ERR_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return ZI_OK;
+}
+
+int noalloc_read_err(int* derr, cudaStream_t s) {
+  int h = 0;
+  ZI_CUDA(cudaMemcpyAsync(&h, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ZI_CUDA(cudaStreamSynchronize(s));
+  return device_error_to_status(h);
+}
+
+}  // namespace
+}  // namespace zi
+
+extern "C" int zi_leadfield_noalloc(zi_system* S, const int32_t* dip_tet, int64_t P, double* Lout, cudaStream_t s) {
+  if (!S) return set_error(ZI_ERR_ARG, "null system");
+  if (P < 0) return set_error(ZI_ERR_ARG, "negative dipole count");
+  if (P > 0 && (!dip_tet || !Lout)) return set_error(ZI_ERR_ARG, "null dipole or output array");
+  if (!S->has_T) return set_error(ZI_ERR_ARG, "the system holds no transfer matrix: run zi_transfer first");
+  if (P == 0) return ZI_OK;
+  const int ncol = S->n_rhs;
+  const bool cem = S->model == ZI_ELECTRODE_CEM;
+  const int L = S->n_el;
+  const size_t avail = NOALLOC_WORDS - NOALLOC_HEAD;
+  const double need = 3.0 * (double)P * ncol + (cem ? 2.0 * (double)L * L : 0.0);
+  if (need > (double)avail)
+    return set_error(ZI_ERR_ARG,
+                     "zi_leadfield_noalloc needs %.0f doubles of scratch for P=%lld and %d rows; the fixed scratch "
+                     "holds %zu (ZI_NOALLOC_SCRATCH_BYTES = %u)",
+                     need, (long long)P, ncol, avail, (unsigned)ZI_NOALLOC_SCRATCH_BYTES);
+  void* base = nullptr;
+  ZI_CHECK(noalloc_scratch(&base));
+  int* err = static_cast<int*>(base);
+  double* Ht = static_cast<double*>(base) + NOALLOC_HEAD;
+  double* Sm = Ht + (size_t)3 * P * ncol;
+  double* Wm = Sm + (size_t)L * L;
+  // the error word keeps the previous call's value: clear it
+  ZI_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  k_source_apply<<<grid_for(P * 32, 256, 152u * 64u), 256, 0, s>>>(P, dip_tet, S->m, S->tets, S->nodes, S->T, ncol,
+                                                                  Ht, err);
+  ZI_LAUNCH_CHECK();
+  ZI_CHECK(noalloc_read_err(err, s));
+  const int64_t N = 3 * P;
+  if (cem) {
+    ZI_CHECK(schur_matrix(S, Sm, s));
+    k_chol_inverse<<<1, 1024, 0, s>>>(L, Sm, Wm, 1, err);
+    ZI_LAUNCH_CHECK();
+    ZI_CHECK(noalloc_read_err(err, s));
+    dim3 grid((unsigned)((N + GT - 1) / GT), (unsigned)((L + GT - 1) / GT));
+    k_gemm_abt<<<grid, 256, 0, s>>>(L, L, N, Wm, Ht, Lout);
+    ZI_LAUNCH_CHECK();
+  } else {
+    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((ncol + 31) / 32));
+    k_transpose<<<grid, dim3(32, 8), 0, s>>>(ncol, N, Ht, Lout);
+    ZI_LAUNCH_CHECK();
+  }
+  ZI_CUDA(cudaStreamSynchronize(s));
+  return ZI_OK;
 }

@@ -28,7 +28,7 @@ EXPORTS = ("zi_version", "zi_last_error", "zi_status_string", "zi_mesh_from_grid
            "zi_locate_dipoles_grid", "zi_assemble", "zi_system_set_conductivity",
            "zi_system_get_info", "zi_system_get_matrix", "zi_system_destroy",
            "zi_solver_opts_default", "zi_transfer", "zi_transfer_batched", "zi_leadfield",
-           "zi_eit_jacobian", "zi_time_spmm", "zi_kernel_launches")
+           "zi_eit_jacobian", "zi_leadfield_noalloc", "zi_time_spmm", "zi_kernel_launches")
 
 
 class ZiError(RuntimeError):
@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "zi_transfer_batched": ([P, ctypes.c_int, ctypes.POINTER(_Opts), P, P, P], ctypes.c_int),
         "zi_leadfield": ([P, P, I64, ctypes.POINTER(_Opts), P, P], ctypes.c_int),
         "zi_eit_jacobian": ([P, P, ctypes.c_int, ctypes.c_int, P, P, P, ctypes.POINTER(_Opts), P], ctypes.c_int),
+        "zi_leadfield_noalloc": ([P, P, I64, P, P], ctypes.c_int),
         "zi_time_spmm": ([P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(D), ctypes.POINTER(D), P], ctypes.c_int),
         "zi_kernel_launches": ([], ctypes.c_int64),
     }
