@@ -247,24 +247,22 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
 // while the current row's gathers are in flight (one memory latency per row),
 // and P[i] for the p.q dot is the slot-0 gather.
 constexpr int ELL_K = 8;
-struct EllRow {
-  int j[ELL_K];
-  float a[ELL_K];
-};
 
-__device__ __forceinline__ void ell_load(const int4* __restrict__ ci, const float4* __restrict__ va, int64_t i,
-                                         EllRow& r) {
+__device__ __forceinline__ void ell_cols(const int4* __restrict__ ci, int64_t i, int (&j)[ELL_K]) {
 #pragma unroll
   for (int q = 0; q < ELL_K / 4; ++q) {
     int4 c = __ldg(ci + i * (ELL_K / 4) + q);
-    float4 v = __ldg(va + i * (ELL_K / 4) + q);
-    r.j[4 * q + 0] = c.x; r.j[4 * q + 1] = c.y; r.j[4 * q + 2] = c.z; r.j[4 * q + 3] = c.w;
-    r.a[4 * q + 0] = v.x; r.a[4 * q + 1] = v.y; r.a[4 * q + 2] = v.z; r.a[4 * q + 3] = v.w;
+    j[4 * q + 0] = c.x; j[4 * q + 1] = c.y; j[4 * q + 2] = c.z; j[4 * q + 3] = c.w;
   }
 }
 
+// Slot 0 holds the diagonal's column i, stored as ~i (negative) when the row
+// continues in the tail.
 template <int CPTV>
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1 ? 3 : 2)
+#ifndef ZI_ELL_MINB
+#define ZI_ELL_MINB 4
+#endif
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1 ? ZI_ELL_MINB : 2)
     k_spmm_ell(int64_t n, int tpr, const int4* __restrict__ ci, const float4* __restrict__ va,
                const int32_t* __restrict__ tail_ptr, const int32_t* __restrict__ tail_ci,
                const float* __restrict__ tail_va, const float* __restrict__ P, float* __restrict__ Q, int ld,
@@ -286,27 +284,33 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
   const RowWalk rw = row_walk(n, rpb, g);
   int64_t i = rw_first(rw);
   bool active = i >= 0;
-  EllRow nxt;
-  if (active) ell_load(ci, va, i, nxt);
+  int jn[ELL_K];
+  if (active) ell_cols(ci, i, jn);
   while (active) {
-    EllRow cur = nxt;
+    int j[ELL_K];
+#pragma unroll
+    for (int u = 0; u < ELL_K; ++u) j[u] = jn[u];
+    const bool tail = j[0] < 0;
+    j[0] = tail ? ~j[0] : j[0];
     V x[ELL_K][CPTV];
 #pragma unroll
     for (int u = 0; u < ELL_K; ++u)
 #pragma unroll
       for (int v = 0; v < CPTV; ++v)
-        x[u][v] = cur.j[u] >= 0 ? ldg_v(Pv + (int64_t)cur.j[u] * nv + v * tpr) : vzero<V>();
+        x[u][v] = j[u] >= 0 ? ldg_v(Pv + (j[u] * nv + v * tpr)) : vzero<V>();  // n*ld/4 < 2^31 (host-checked)
+    const float4 a0 = __ldg(va + i * (ELL_K / 4)), a1 = __ldg(va + i * (ELL_K / 4) + 1);
     const int64_t inext = rw_next(rw, i);
     const bool more = inext >= 0;
-    if (more) ell_load(ci, va, inext, nxt);
+    if (more) ell_cols(ci, inext, jn);
+    const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
     V acc[CPTV];
 #pragma unroll
     for (int v = 0; v < CPTV; ++v) {
       acc[v] = vzero<V>();
 #pragma unroll
-      for (int u = 0; u < ELL_K; ++u) vfma(acc[v], cur.a[u], x[u][v]);
+      for (int u = 0; u < ELL_K; ++u) vfma(acc[v], a[u], x[u][v]);
     }
-    if (tail_ptr) {
+    if (tail) {
       const int t0 = __ldg(tail_ptr + i), t1 = __ldg(tail_ptr + i + 1);
       for (int t = t0; t < t1; ++t) {
         const int jj = __ldg(tail_ci + t);
@@ -628,6 +632,7 @@ __global__ void k_fill_ell(int64_t n, const int32_t* __restrict__ rowptr32, cons
       cr[o] = -1;
       vr[o] = 0.f;
     }
+    if (tail_ptr && tail_ptr[i + 1] > tail_ptr[i]) cr[0] = ~(int32_t)i;
   }
 }
 
@@ -876,7 +881,7 @@ constexpr int BLOCK = 256;
 
 int blocks_per_sm_for(int tpr) {
   (void)tpr;
-  return 4;
+  return 8;
 }
 
 template <typename T>
@@ -956,6 +961,7 @@ int launch_residual(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, 
 struct CgPlan {
   int64_t n;
   int ld, ncol, tpr, cptv, nblk;
+  int g_spmm = 0, g_resid = 0, g_dir = 0;  // resident-grid sizes of the per-iteration kernels
   size_t smem;
   const int32_t* rowptr;
   const int32_t* colind;
@@ -966,15 +972,93 @@ struct CgPlan {
   const float* tail_va = nullptr;
 };
 
+// Grid of a per-iteration kernel: every block resident at once (so the whole
+// grid sweeps the rows together), a multiple of CLUSTER for the clustered
+// kernels, at most `cap` blocks (the size of the partial buffers).
+static int resident_grid(const void* fn, size_t smem, bool clustered, int cap) {
+  int g = 0;
+  if (clustered) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CLUSTER * 64);
+    cfg.blockDim = dim3(BLOCK);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = CLUSTER;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) == cudaSuccess && ncl > 0) g = ncl * CLUSTER;
+    (void)cudaGetLastError();
+  }
+  if (g == 0) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BLOCK, smem) != cudaSuccess || occ < 1) occ = 1;
+    (void)cudaGetLastError();
+    g = sm_count() * occ;
+    if (clustered) g = g / CLUSTER * CLUSTER;
+  }
+  if (g > cap) g = cap / (clustered ? CLUSTER : 1) * (clustered ? CLUSTER : 1);
+  if (g < CLUSTER) g = CLUSTER;
+  return g;
+}
+
+template <typename T>
+static const void* spmm_fn(int cptv, bool ell) {
+  if constexpr (sizeof(T) == 4) {
+    if (ell) {
+      switch (cptv) {
+        case 1: return (const void*)k_spmm_ell<1>;
+        case 2: return (const void*)k_spmm_ell<2>;
+        case 4: return (const void*)k_spmm_ell<4>;
+      }
+    }
+  }
+  switch (cptv) {
+    case 1: return (const void*)k_spmm_dot<T, 1>;
+    case 2: return (const void*)k_spmm_dot<T, 2>;
+    case 4: return (const void*)k_spmm_dot<T, 4>;
+    default: return (const void*)k_spmm_dot<T, 8>;
+  }
+}
+template <typename T>
+static const void* resid_fn(int cptv) {
+  switch (cptv) {
+    case 1: return (const void*)k_cg_resid<T, 1>;
+    case 2: return (const void*)k_cg_resid<T, 2>;
+    case 4: return (const void*)k_cg_resid<T, 4>;
+    default: return (const void*)k_cg_resid<T, 8>;
+  }
+}
+template <typename T>
+static const void* dir_fn(int cptv) {
+  switch (cptv) {
+    case 1: return (const void*)k_cg_dir<T, 1>;
+    case 2: return (const void*)k_cg_dir<T, 2>;
+    case 4: return (const void*)k_cg_dir<T, 4>;
+    default: return (const void*)k_cg_dir<T, 8>;
+  }
+}
+
+template <typename T>
+static void size_grids(CgPlan& p) {
+  const bool ell = sizeof(T) == 4 && p.ell_ci && p.cptv <= 4;
+  p.g_spmm = resident_grid(spmm_fn<T>(p.cptv, ell), p.smem, true, p.nblk);
+  p.g_resid = resident_grid(resid_fn<T>(p.cptv), p.smem, true, p.nblk);
+  p.g_dir = resident_grid(dir_fn<T>(p.cptv), 0, false, 1 << 20);
+}
+
 // The SpMM of one CG iteration: ELL for the FP32 matrix when available.
 template <typename T>
 static int plan_spmm(const CgPlan& p, const T* vals, const T* P, T* Q, double* part, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
     if (p.ell_ci && p.cptv <= 4)
-      return launch_spmm_ell(p.cptv, dim3(p.nblk), p.tpr, p.smem, st, p.n, p.ell_ci, p.ell_va, p.tail_ptr,
+      return launch_spmm_ell(p.cptv, dim3(p.g_spmm), p.tpr, p.smem, st, p.n, p.ell_ci, p.ell_va, p.tail_ptr,
                              p.tail_ci, p.tail_va, P, Q, p.ld, part);
   }
-  return launch_spmm<T>(p.cptv, dim3(p.nblk), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, vals, P, Q, p.ld, part);
+  return launch_spmm<T>(p.cptv, dim3(p.g_spmm), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, vals, P, Q, p.ld, part);
 }
 
 static CgPlan make_plan(zi_system* S, SolverScratch* w, int cptv, int vecw) {
@@ -998,17 +1082,17 @@ static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T
                              cudaStream_t st) {
   ColState cs{w->rho, w->alpha, w->beta, w->stop2, w->conv, w->iters, w->cnt, w->cnt + 1, w->cnt + 2,
               sizeof(T) == sizeof(double) ? 1 : 0};
-  dim3 grid(p.nblk);
-  const int ncl = p.nblk / CLUSTER;  // partials per reduction: one per cluster
+  // partials per reduction: one per cluster of each kernel's resident grid
+  const int ncl_spmm = p.g_spmm / CLUSTER, ncl_resid = p.g_resid / CLUSTER;
   for (int k = 0; k < chunk; ++k) {
     ZI_CHECK(plan_spmm<T>(p, vals, P, Q, w->part0, st));
-    k_fin_alpha<<<1, FIN_THREADS, 0, st>>>(ncl, p.ld, p.ncol, w->part0, cs);
+    k_fin_alpha<<<1, FIN_THREADS, 0, st>>>(ncl_spmm, p.ld, p.ncol, w->part0, cs);
     ZI_LAUNCH_CHECK();
-    ZI_CHECK(launch_resid<T>(p.cptv, grid, p.tpr, p.smem, st, p.n, p.ld, w->alpha, Q, R, w->dtrue, w->part1,
-                             w->part2));
-    k_fin_beta<<<1, FIN_THREADS, 0, st>>>(ncl, p.ld, p.ncol, w->part1, w->part2, cs);
+    ZI_CHECK(launch_resid<T>(p.cptv, dim3(p.g_resid), p.tpr, p.smem, st, p.n, p.ld, w->alpha, Q, R, w->dtrue,
+                             w->part1, w->part2));
+    k_fin_beta<<<1, FIN_THREADS, 0, st>>>(ncl_resid, p.ld, p.ncol, w->part1, w->part2, cs);
     ZI_LAUNCH_CHECK();
-    ZI_CHECK(launch_dir<T>(p.cptv, grid, p.tpr, st, p.n, p.ld, w->alpha, w->beta, R, P, X));
+    ZI_CHECK(launch_dir<T>(p.cptv, dim3(p.g_dir), p.tpr, st, p.n, p.ld, w->alpha, w->beta, R, P, X));
   }
   return ZI_OK;
 }
@@ -1182,6 +1266,7 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
   int ld_, c64, c32;
   choose_layout(ncol, &ld_, &c64, &c32);
   CgPlan p64 = make_plan(S, w, c64, 2);
+  size_grids<double>(p64);
   CgPlan p32 = make_plan(S, w, c32, 4);
   p32.rowptr = w->rowptr32;
   p32.colind = w->colind32;
@@ -1314,7 +1399,7 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
     ZI_LAUNCH_CHECK();
   } else {
     // FP64 outer: X64 (original space, w->X) = 0, R64 = B
-    const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
+    const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-1;
     const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
     ZI_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n * ld, st));
     // |b|^2 per column (and R64 = B padded, via the residual of X = 0)
@@ -1364,6 +1449,7 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
       p32.tail_ptr = w->tail_ptr;
       p32.tail_ci = w->tail_ci;
       p32.tail_va = w->tail_va;
+      if (!p32.g_spmm) size_grids<float>(p32);
       int ran = 0;
       int st2 = run_cg<float>(p32, w, w->v32, w->x32, w->r32, w->p32, w->q32, o->maxit - total, chunk,
                               &w->graph32, &w->graph_chunk32, &ran);
@@ -1411,7 +1497,7 @@ extern "C" void zi_solver_opts_default(zi_solver_opts* o) {
   o->maxit = 100000;
   o->precond = ZI_PRECOND_JACOBI;
   o->precision = ZI_FP64;
-  o->inner_tol = 1e-4;
+  o->inner_tol = 1e-1;
   o->max_outer = 30;
   o->check_every = 25;
 }
@@ -1476,6 +1562,9 @@ extern "C" int zi_time_spmm(zi_system* S, int precision, int reps, double* ms_pe
     p.tail_ptr = w->tail_ptr;
     p.tail_ci = w->tail_ci;
     p.tail_va = w->tail_va;
+    size_grids<float>(p);
+  } else {
+    size_grids<double>(p);
   }
   cudaStream_t st = w->stream;
   const int64_t nflush = 64ll << 20;  // 64 Mi floats = 256 MB
