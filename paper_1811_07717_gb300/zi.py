@@ -231,6 +231,7 @@ class System:
                                _ptr(s6), _ptr(self.bfaces), self.bfaces.shape[0], ctypes.byref(el),
                                ctypes.byref(h), _stream()))
         self._h = h
+        self.version = 0  # bumped whenever the matrix values change
 
     @property
     def handle(self):
@@ -262,6 +263,7 @@ class System:
         torch = _torch()
         s6 = _dev(sigma6, torch.float64)
         _check(self._lib.zi_system_set_conductivity(self._h, _ptr(s6), _stream()))
+        self.version += 1
 
     def transfer(self, opts: SolverOpts | None = None, want_T: bool = True, allow_not_converged=False):
         """T = A^-1 B (zi_transfer); returns (T or None, iters, relres)."""
