@@ -119,17 +119,23 @@ __device__ __forceinline__ void cluster_column_store(double* stot, int ld, doubl
 struct RowWalk {
   int64_t n;
   int C, rpb, g;
+  int blk, nblk;  // this block's index among the nblk blocks sharing the rows
 };
-__device__ __forceinline__ RowWalk row_walk(int64_t n, int rpb, int g) { return RowWalk{n, 4 * rpb, rpb, g}; }
+__device__ __forceinline__ RowWalk row_walk(int64_t n, int rpb, int g) {
+  return RowWalk{n, 4 * rpb, rpb, g, (int)blockIdx.x, (int)gridDim.x};
+}
+__device__ __forceinline__ RowWalk row_walk_sub(int64_t n, int rpb, int g, int blk, int nblk) {
+  return RowWalk{n, 4 * rpb, rpb, g, blk, nblk};
+}
 __device__ __forceinline__ int64_t rw_first(const RowWalk& w) {
-  int64_t i = (int64_t)blockIdx.x * w.C + w.g;
+  int64_t i = (int64_t)w.blk * w.C + w.g;
   return (w.g < w.rpb && i < w.n) ? i : -1;
 }
 __device__ __forceinline__ int64_t rw_next(const RowWalk& w, int64_t i) {
   int64_t base = i - i % w.C;
   int64_t nx = i + w.rpb;
   if (nx < base + w.C) return nx < w.n ? nx : -1;
-  nx = base + (int64_t)gridDim.x * w.C + w.g;
+  nx = base + (int64_t)w.nblk * w.C + w.g;
   return nx < w.n ? nx : -1;
 }
 
@@ -826,7 +832,10 @@ struct SolverScratch {
   double *part0 = nullptr, *part1 = nullptr, *part2 = nullptr;
   // column state (ld each)
   double *rho = nullptr, *alpha = nullptr, *beta = nullptr, *stop2 = nullptr, *bb = nullptr, *vec = nullptr;
-  int *conv = nullptr, *iters = nullptr, *cnt = nullptr;  // cnt[0] active, cnt[1] iteration
+  int *conv = nullptr, *iters = nullptr, *cnt = nullptr;  // cnt[0] active, cnt[1] iteration, cnt[2] reached
+  double *gamma = nullptr, *gamma_prev = nullptr;  // mixed: column scale of the FP32 phase
+  int *flag = nullptr, *nact = nullptr;            // mixed: columns within tol / count
+  unsigned* bar = nullptr;                         // batched: per-head barrier (arrivals, generation)
   bool values_ready = false;   // s, dtrue, v64 match the system's values
   bool v32_ready = false;      // v32 matches
   cudaStream_t stream = nullptr;
@@ -847,7 +856,7 @@ void solver_scratch_free(zi_system* S) {
   cudaStream_t s = 0;
   void* ptrs[] = {w->s, w->dtrue, w->ones, w->v64, w->v32, w->rowptr32, w->colind32, w->ell_ci, w->ell_va, w->tail_ptr, w->tail_ci, w->tail_va, w->X, w->R, w->P, w->Q, w->x32, w->r32, w->p32, w->q32,
                   w->part0, w->part1, w->part2, w->rho, w->alpha, w->beta, w->stop2, w->bb, w->vec,
-                  w->conv, w->iters, w->cnt};
+                  w->conv, w->iters, w->cnt, w->gamma, w->gamma_prev, w->flag, w->nact, w->bar};
   for (void* p : ptrs) dfree(p, s);
   if (w->graph64) cudaGraphExecDestroy(w->graph64);
   if (w->graph32) cudaGraphExecDestroy(w->graph32);
@@ -1184,6 +1193,10 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
     ZI_CHECK(dalloc_n(&w->conv, ld, s));
     ZI_CHECK(dalloc_n(&w->iters, ld, s));
     ZI_CHECK(dalloc_n(&w->cnt, 3, s));
+    ZI_CHECK(dalloc_n(&w->gamma, ld, s));
+    ZI_CHECK(dalloc_n(&w->gamma_prev, ld, s));
+    ZI_CHECK(dalloc_n(&w->flag, ld, s));
+    ZI_CHECK(dalloc_n(&w->nact, 1, s));
   }
   if (mixed && !w->x32) {
     int64_t nl = S->n * (int64_t)w->ld;
@@ -1248,32 +1261,32 @@ __global__ void k_flags_from_res(int ld, int ncol, const double* __restrict__ rr
   if (threadIdx.x == 0) *nact = a;
 }
 
-int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* iters, double* relres,
-                  cudaStream_t user) {
+// ---------------------------------------------------------------------------
+// One head's solve as a sequence of steps, shared by the single-system path
+// (iterations replayed from a CUDA graph) and the batched path (iterations of
+// all heads in one persistent launch).
+// ---------------------------------------------------------------------------
+
+struct HeadRun {
+  zi_system* S = nullptr;
+  const zi_solver_opts* o = nullptr;
+  cudaStream_t st = nullptr;
+  bool mixed = false, done = false;
+  int status = ZI_OK;
+  int c64 = 1, c32 = 1;
+  CgPlan p64, p32;
+  std::vector<int> iters;
+  std::vector<double> relres;
+  int total = 0, outer = 0, restart = 0;
+};
+
+int mixed_phase_begin(HeadRun& h);
+
+// Scaled FP64 matrix, and the FP32 CSR / ELL copies for the mixed path.
+static int prepare_matrices(zi_system* S, const zi_solver_opts* o, cudaStream_t st) {
   SolverScratch* w = S->solver;
   const bool mixed = o->precision == ZI_MIXED;
-  ZI_CHECK(ensure_scratch(S, o, user));
-  w = S->solver;
-  cudaStream_t st = w->stream;
-  // order the internal stream after the caller's stream
-  cudaEvent_t ev;
-  ZI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-  ZI_CUDA(cudaEventRecord(ev, user));
-  ZI_CUDA(cudaStreamWaitEvent(st, ev, 0));
-
   const int64_t n = S->n;
-  const int ld = w->ld, ncol = S->n_rhs;
-  int ld_, c64, c32;
-  choose_layout(ncol, &ld_, &c64, &c32);
-  CgPlan p64 = make_plan(S, w, c64, 2);
-  size_grids<double>(p64);
-  CgPlan p32 = make_plan(S, w, c32, 4);
-  p32.rowptr = w->rowptr32;
-  p32.colind = w->colind32;
-  const int nblk = w->nblk;
-  const int chunk = o->check_every > 0 ? o->check_every : 25;
-
-  // scaling and scaled matrices (once per set of values)
   if (!w->values_ready || w->precond != o->precond) {
     k_scale<<<grid_for(n, 256), 256, 0, st>>>(n, o->precond, S->rowptr, S->colind, S->vals, S->diagpos, w->s,
                                               w->dtrue);
@@ -1329,14 +1342,48 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
     w->ntail = ntail;
     w->v32_ready = true;
   }
-  const double tol2 = o->tol * o->tol;
-  const size_t smem_init = sizeof(double) * (size_t)(BLOCK / ld > 0 ? BLOCK / ld : 1) * ld;
+  return ZI_OK;
+}
+
+int head_begin(HeadRun& h) {
+  zi_system* S = h.S;
+  const zi_solver_opts* o = h.o;
+  h.mixed = o->precision == ZI_MIXED;
+  ZI_CHECK(ensure_scratch(S, o, h.st));
+  SolverScratch* w = S->solver;
+  const cudaStream_t st = h.st;
+  const int64_t n = S->n;
+  const int ld = w->ld, ncol = S->n_rhs;
   if (ld > BLOCK) return set_error(ZI_ERR_ARG, "more than %d right-hand sides per system", BLOCK);
-
-  std::vector<int> h_iters(ld, 0);
-  int status = ZI_OK;
-
-  if (!mixed) {
+  int ld_, c64, c32;
+  choose_layout(ncol, &ld_, &c64, &c32);
+  h.c64 = c64;
+  h.c32 = c32;
+  ZI_CHECK(prepare_matrices(S, o, st));
+  h.p64 = make_plan(S, w, c64, 2);
+  size_grids<double>(h.p64);
+  h.p32 = make_plan(S, w, c32, 4);
+  h.p32.rowptr = w->rowptr32;
+  h.p32.colind = w->colind32;
+  if (h.mixed) {
+    h.p32.ell_ci = w->ell_ci;
+    h.p32.ell_va = w->ell_va;
+    h.p32.tail_ptr = w->tail_ptr;
+    h.p32.tail_ci = w->tail_ci;
+    h.p32.tail_va = w->tail_va;
+    size_grids<float>(h.p32);
+  }
+  h.iters.assign(ld, 0);
+  h.relres.assign(ncol, 0.0);
+  h.total = 0;
+  h.outer = 0;
+  h.restart = 0;
+  h.done = false;
+  h.status = ZI_OK;
+  const int nblk = w->nblk;
+  const double tol2 = o->tol * o->tol;
+  const size_t smem_init = sizeof(double) * (size_t)(BLOCK / ld) * ld;
+  if (!h.mixed) {
     // r~ = S b, x~ = 0, p = r~
     k_init_rhs<<<nblk, BLOCK, smem_init, st>>>(n, ncol, ld, S->B, w->s, w->R, w->part1, w->part0);
     ZI_LAUNCH_CHECK();
@@ -1345,145 +1392,617 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
     ZI_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n * ld, st));
     ZI_CUDA(cudaMemcpyAsync(w->P, w->R, sizeof(double) * n * ld, cudaMemcpyDeviceToDevice, st));
     k_init_cols<<<1, FIN_THREADS, 0, st>>>(nblk, ld, ncol, w->part0, w->bb, tol2, nullptr, w->rho, w->stop2, w->conv,
-                                   w->iters, w->cnt);
+                                           w->iters, w->cnt);
     ZI_LAUNCH_CHECK();
-    int total = 0;
-    for (int restart = 0; restart < 4; ++restart) {
-      int ran = 0;
-      ZI_CHECK(run_cg<double>(p64, w, w->v64, w->X, w->R, w->P, w->Q, o->maxit - total, chunk, &w->graph64,
-                              &w->graph_chunk64, &ran));
-      std::vector<int> it(ld);
-      ZI_CUDA(cudaMemcpyAsync(it.data(), w->iters, sizeof(int) * ld, cudaMemcpyDeviceToHost, st));
-      ZI_CUDA(cudaStreamSynchronize(st));
-      for (int c = 0; c < ncol; ++c) h_iters[c] += it[c];
-      total += ran;
-      // true residual in the original space: R0 = B - A (S x~)
-      k_unscale_out<<<grid_for(n * ld, 256), 256, 0, st>>>(n, ncol, ld, w->s, w->X, w->Q, nullptr);
-      ZI_LAUNCH_CHECK();
-      ZI_CHECK(launch_residual(c64, dim3(nblk), p64.tpr, p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
-                               w->Q, S->B, w->P, w->part0));
-      k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part0, w->vec);
-      ZI_LAUNCH_CHECK();
-      std::vector<double> rr(ld), bb(ld);
-      ZI_CUDA(cudaMemcpyAsync(rr.data(), w->vec, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
-      ZI_CUDA(cudaMemcpyAsync(bb.data(), w->bb, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
-      ZI_CUDA(cudaStreamSynchronize(st));
-      bool all = true;
-      for (int c = 0; c < ncol; ++c) {
-        double rel = bb[c] > 0 ? sqrt(rr[c] / bb[c]) : 0.0;
-        if (relres) relres[c] = rel;
-        if (!(rel <= o->tol)) all = false;
-      }
-      if (all || total >= o->maxit) {
-        status = all ? ZI_OK : set_error(ZI_ERR_NOT_CONVERGED, "PCG reached maxit=%d before tol=%g", o->maxit, o->tol);
-        break;
-      }
-      // residual replacement: r~ = S r_true, p = r~, restart the recurrence on
-      // the columns that drifted
-      // r~ = S R0 (R0 is the padded n x ld residual in w->P)
-      k_init_rhs<<<nblk, BLOCK, smem_init, st>>>(n, ld, ld, w->P, w->s, w->R, w->part2, w->part0);
-      ZI_LAUNCH_CHECK();
-      ZI_CUDA(cudaMemcpyAsync(w->P, w->R, sizeof(double) * n * ld, cudaMemcpyDeviceToDevice, st));
-      // keep the original |b|^2 in w->bb; skip columns already within tol
-      std::vector<int> skip(ld, 1);
-      for (int c = 0; c < ncol; ++c) skip[c] = (bb[c] > 0 && sqrt(rr[c] / bb[c]) <= o->tol) ? 1 : 0;
-      ZI_CUDA(cudaMemcpyAsync(w->conv, skip.data(), sizeof(int) * ld, cudaMemcpyHostToDevice, st));
-      // conv doubles as the skip list for k_init_cols (read before written)
-      k_init_cols<<<1, FIN_THREADS, 0, st>>>(nblk, ld, ncol, w->part0, w->bb, tol2, w->conv, w->rho, w->stop2, w->conv,
-                                     w->iters, w->cnt);
-      ZI_LAUNCH_CHECK();
-      ZI_CUDA(cudaStreamSynchronize(st));
-    }
-    // T = S x~
-    k_unscale_out<<<grid_for(n * ld, 256), 256, 0, st>>>(n, ncol, ld, w->s, w->X, nullptr, S->T);
+    return ZI_OK;
+  }
+  // mixed: FP64 outer X64 (original space, w->X) = 0, R64 = B; |b|^2 per column
+  ZI_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n * ld, st));
+  ZI_CHECK(launch_residual(c64, dim3(nblk), h.p64.tpr, h.p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
+                           w->X, S->B, w->R, w->part0));
+  k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part0, w->bb);
+  ZI_LAUNCH_CHECK();
+  ZI_CUDA(cudaMemcpyAsync(w->vec, w->bb, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st));
+  ZI_CUDA(cudaMemsetAsync(w->gamma, 0, sizeof(double) * ld, st));
+  return mixed_phase_begin(h);
+}
+
+// Mixed path: start an FP32 phase from the FP64 residual in w->R (|R|^2 in
+// w->vec), or finish when every column meets tol.
+int mixed_phase_begin(HeadRun& h) {
+  zi_system* S = h.S;
+  SolverScratch* w = S->solver;
+  const zi_solver_opts* o = h.o;
+  const cudaStream_t st = h.st;
+  const int64_t n = S->n;
+  const int ld = w->ld, ncol = S->n_rhs, nblk = w->nblk;
+  const double tol2 = o->tol * o->tol;
+  const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-1;
+  const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
+  const size_t smem_init = sizeof(double) * (size_t)(BLOCK / ld) * ld;
+  ZI_CUDA(cudaMemcpyAsync(w->gamma_prev, w->gamma, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st));
+  k_flags_from_res<<<1, FIN_THREADS, 0, st>>>(ld, ncol, w->vec, w->bb, tol2, w->flag, w->gamma, w->nact);
+  ZI_LAUNCH_CHECK();
+  int hn = 0;
+  std::vector<double> rr(ld), bb(ld);
+  ZI_CUDA(cudaMemcpyAsync(&hn, w->nact, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ZI_CUDA(cudaMemcpyAsync(rr.data(), w->vec, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
+  ZI_CUDA(cudaMemcpyAsync(bb.data(), w->bb, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
+  ZI_CUDA(cudaStreamSynchronize(st));
+  for (int c = 0; c < ncol; ++c) h.relres[c] = bb[c] > 0 ? sqrt(rr[c] / bb[c]) : 0.0;
+  if (hn == 0) {
+    h.done = true;
+    h.status = ZI_OK;
+    return ZI_OK;
+  }
+  if (h.outer >= max_outer || h.total >= o->maxit) {
+    h.done = true;
+    h.status = set_error(ZI_ERR_NOT_CONVERGED, "mixed-precision refinement missed tol=%g", o->tol);
+    return ZI_OK;
+  }
+  // inner right-hand side r~32 = S R64 / |R64|, x32 = 0, p32 = r~32 (kept and
+  // rescaled after the first phase)
+  k_prep_inner<<<nblk, BLOCK, smem_init, st>>>(n, ld, w->s, w->R, w->gamma, w->gamma_prev, h.outer > 0 ? 1 : 0,
+                                               w->r32, w->x32, w->p32, w->part0);
+  ZI_LAUNCH_CHECK();
+  k_init_cols<<<1, FIN_THREADS, 0, st>>>(nblk, ld, ncol, w->part0, nullptr, itol * itol, w->flag, w->rho, w->stop2,
+                                         w->conv, w->iters, w->cnt);
+  ZI_LAUNCH_CHECK();
+  ++h.outer;
+  return ZI_OK;
+}
+
+// After a run of CG iterations (`ran` of them): FP64 -> check the true
+// residual, restart drifted columns or finish; mixed -> reliable update.
+int head_after_inner(HeadRun& h, int ran) {
+  zi_system* S = h.S;
+  SolverScratch* w = S->solver;
+  const zi_solver_opts* o = h.o;
+  const cudaStream_t st = h.st;
+  const int64_t n = S->n;
+  const int ld = w->ld, ncol = S->n_rhs, nblk = w->nblk;
+  const double tol2 = o->tol * o->tol;
+  const size_t smem_init = sizeof(double) * (size_t)(BLOCK / ld) * ld;
+  std::vector<int> it(ld);
+  ZI_CUDA(cudaMemcpyAsync(it.data(), w->iters, sizeof(int) * ld, cudaMemcpyDeviceToHost, st));
+  ZI_CUDA(cudaStreamSynchronize(st));
+  for (int c = 0; c < ncol; ++c) h.iters[c] += it[c];
+  h.total += ran;
+  if (h.mixed) {
+    // X64 += gamma * S * x32 ; R64 = B - A X64
+    k_accumulate<<<grid_for(n * ld, 256), 256, 0, st>>>(n, ld, w->s, w->gamma, w->x32, w->X);
     ZI_LAUNCH_CHECK();
-  } else {
-    // FP64 outer: X64 (original space, w->X) = 0, R64 = B
-    const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-1;
-    const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
-    ZI_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n * ld, st));
-    // |b|^2 per column (and R64 = B padded, via the residual of X = 0)
-    ZI_CHECK(launch_residual(c64, dim3(nblk), p64.tpr, p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
-                             w->X, S->B, w->R, w->part0));
-    k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part0, w->bb);
+    ZI_CHECK(launch_residual(h.c64, dim3(nblk), h.p64.tpr, h.p64.smem, st, n, ncol, ld, S->rowptr, S->colind,
+                             S->vals, w->X, S->B, w->R, w->part0));
+    k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part0, w->vec);
     ZI_LAUNCH_CHECK();
-    ZI_CUDA(cudaMemcpyAsync(w->vec, w->bb, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st));
-    // the inner recurrence stops on the scaled-space norm |r~32| (weights 1)
-    DevTmp<int> flag, nact;
-    DevTmp<double> gamma, gamma_prev;
-    ZI_CHECK(flag.alloc(ld, st));
-    ZI_CHECK(nact.alloc(1, st));
-    ZI_CHECK(gamma.alloc(ld, st));
-    ZI_CHECK(gamma_prev.alloc(ld, st));
-    ZI_CUDA(cudaMemsetAsync(gamma.p, 0, sizeof(double) * ld, st));
-    double* dtrue_saved = w->dtrue;
-    int total = 0;
-    bool all = false;
-    for (int outer = 0; outer <= max_outer; ++outer) {
-      // w->vec holds |R64|^2 per column
-      ZI_CUDA(cudaMemcpyAsync(gamma_prev.p, gamma.p, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st));
-      k_flags_from_res<<<1, FIN_THREADS, 0, st>>>(ld, ncol, w->vec, w->bb, tol2, flag.p, gamma.p, nact.p);
-      ZI_LAUNCH_CHECK();
-      int hn = 0;
-      std::vector<double> rr(ld), bb(ld);
-      ZI_CUDA(cudaMemcpyAsync(&hn, nact.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-      ZI_CUDA(cudaMemcpyAsync(rr.data(), w->vec, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
-      ZI_CUDA(cudaMemcpyAsync(bb.data(), w->bb, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
-      ZI_CUDA(cudaStreamSynchronize(st));
-      for (int c = 0; c < ncol && relres; ++c) relres[c] = bb[c] > 0 ? sqrt(rr[c] / bb[c]) : 0.0;
-      if (hn == 0) {
-        all = true;
-        break;
-      }
-      if (outer == max_outer || total >= o->maxit) break;
-      // inner right-hand side r~32 = S R64 / |R64|, x32 = 0, p32 = r~32
-      k_prep_inner<<<nblk, BLOCK, smem_init, st>>>(n, ld, w->s, w->R, gamma.p, gamma_prev.p, outer > 0 ? 1 : 0,
-                                                   w->r32, w->x32, w->p32, w->part0);
-      ZI_LAUNCH_CHECK();
-      k_init_cols<<<1, FIN_THREADS, 0, st>>>(nblk, ld, ncol, w->part0, nullptr, itol * itol, flag.p, w->rho, w->stop2,
-                                     w->conv, w->iters, w->cnt);
-      ZI_LAUNCH_CHECK();
-      w->dtrue = w->ones;
-      p32.ell_ci = w->ell_ci;
-      p32.ell_va = w->ell_va;
-      p32.tail_ptr = w->tail_ptr;
-      p32.tail_ci = w->tail_ci;
-      p32.tail_va = w->tail_va;
-      if (!p32.g_spmm) size_grids<float>(p32);
-      int ran = 0;
-      int st2 = run_cg<float>(p32, w, w->v32, w->x32, w->r32, w->p32, w->q32, o->maxit - total, chunk,
-                              &w->graph32, &w->graph_chunk32, &ran);
-      w->dtrue = dtrue_saved;
-      ZI_CHECK(st2);
-      std::vector<int> it(ld);
-      ZI_CUDA(cudaMemcpyAsync(it.data(), w->iters, sizeof(int) * ld, cudaMemcpyDeviceToHost, st));
-      ZI_CUDA(cudaStreamSynchronize(st));
-      for (int c = 0; c < ncol; ++c) h_iters[c] += it[c];
-      total += ran;
-      // X64 += gamma * S * x32 ; R64 = B - A X64
-      k_accumulate<<<grid_for(n * ld, 256), 256, 0, st>>>(n, ld, w->s, gamma.p, w->x32, w->X);
-      ZI_LAUNCH_CHECK();
-      ZI_CHECK(launch_residual(c64, dim3(nblk), p64.tpr, p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
-                               w->X, S->B, w->R, w->part0));
-      k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part0, w->vec);
-      ZI_LAUNCH_CHECK();
-    }
+    return mixed_phase_begin(h);
+  }
+  // true residual in the original space: R0 = B - A (S x~)
+  k_unscale_out<<<grid_for(n * ld, 256), 256, 0, st>>>(n, ncol, ld, w->s, w->X, w->Q, nullptr);
+  ZI_LAUNCH_CHECK();
+  ZI_CHECK(launch_residual(h.c64, dim3(nblk), h.p64.tpr, h.p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
+                           w->Q, S->B, w->P, w->part0));
+  k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part0, w->vec);
+  ZI_LAUNCH_CHECK();
+  std::vector<double> rr(ld), bb(ld);
+  ZI_CUDA(cudaMemcpyAsync(rr.data(), w->vec, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
+  ZI_CUDA(cudaMemcpyAsync(bb.data(), w->bb, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
+  ZI_CUDA(cudaStreamSynchronize(st));
+  bool all = true;
+  for (int c = 0; c < ncol; ++c) {
+    double rel = bb[c] > 0 ? sqrt(rr[c] / bb[c]) : 0.0;
+    h.relres[c] = rel;
+    if (!(rel <= o->tol)) all = false;
+  }
+  if (all || h.total >= o->maxit || h.restart >= 3) {
+    h.done = true;
+    h.status = all ? ZI_OK : set_error(ZI_ERR_NOT_CONVERGED, "PCG reached maxit=%d before tol=%g", o->maxit, o->tol);
+    return ZI_OK;
+  }
+  // residual replacement: r~ = S r_true, p = r~; restart the columns that drifted
+  ++h.restart;
+  k_init_rhs<<<nblk, BLOCK, smem_init, st>>>(n, ld, ld, w->P, w->s, w->R, w->part2, w->part0);
+  ZI_LAUNCH_CHECK();
+  ZI_CUDA(cudaMemcpyAsync(w->P, w->R, sizeof(double) * n * ld, cudaMemcpyDeviceToDevice, st));
+  std::vector<int> skip(ld, 1);
+  for (int c = 0; c < ncol; ++c) skip[c] = (bb[c] > 0 && sqrt(rr[c] / bb[c]) <= o->tol) ? 1 : 0;
+  ZI_CUDA(cudaMemcpyAsync(w->conv, skip.data(), sizeof(int) * ld, cudaMemcpyHostToDevice, st));
+  // conv doubles as the skip list for k_init_cols (read before written)
+  k_init_cols<<<1, FIN_THREADS, 0, st>>>(nblk, ld, ncol, w->part0, w->bb, tol2, w->conv, w->rho, w->stop2, w->conv,
+                                         w->iters, w->cnt);
+  ZI_LAUNCH_CHECK();
+  ZI_CUDA(cudaStreamSynchronize(st));
+  return ZI_OK;
+}
+
+int head_finish(HeadRun& h, double* Tout, int32_t* iters, double* relres) {
+  zi_system* S = h.S;
+  SolverScratch* w = S->solver;
+  const cudaStream_t st = h.st;
+  const int64_t n = S->n;
+  const int ld = w->ld, ncol = S->n_rhs;
+  if (h.mixed) {
     // T = X64 (already in the original space)
     ZI_CUDA(cudaMemcpy2DAsync(S->T, sizeof(double) * ncol, w->X, sizeof(double) * ld, sizeof(double) * ncol, n,
                               cudaMemcpyDeviceToDevice, st));
-    status = all ? ZI_OK
-                 : set_error(ZI_ERR_NOT_CONVERGED, "mixed-precision refinement missed tol=%g", o->tol);
+  } else {
+    // T = S x~
+    k_unscale_out<<<grid_for(n * ld, 256), 256, 0, st>>>(n, ncol, ld, w->s, w->X, nullptr, S->T);
+    ZI_LAUNCH_CHECK();
   }
-  if (Tout)
-    ZI_CUDA(cudaMemcpyAsync(Tout, S->T, sizeof(double) * n * ncol, cudaMemcpyDeviceToDevice, st));
+  if (Tout) ZI_CUDA(cudaMemcpyAsync(Tout, S->T, sizeof(double) * n * ncol, cudaMemcpyDeviceToDevice, st));
+  if (iters)
+    for (int c = 0; c < ncol; ++c) iters[c] = h.iters[c];
+  if (relres)
+    for (int c = 0; c < ncol; ++c) relres[c] = h.relres[c];
+  S->has_T = 1;
+  return ZI_OK;
+}
+
+int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* iters, double* relres,
+                  cudaStream_t user) {
+  ZI_CHECK(ensure_scratch(S, o, user));
+  SolverScratch* w = S->solver;
+  cudaStream_t st = w->stream;
+  // order the internal stream after the caller's stream
+  cudaEvent_t ev;
+  ZI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  ZI_CUDA(cudaEventRecord(ev, user));
+  ZI_CUDA(cudaStreamWaitEvent(st, ev, 0));
+  HeadRun h;
+  h.S = S;
+  h.o = o;
+  h.st = st;
+  ZI_CHECK(head_begin(h));
+  const int chunk = o->check_every > 0 ? o->check_every : 25;
+  while (!h.done) {
+    int ran = 0;
+    if (h.mixed) {
+      double* dtrue_saved = w->dtrue;
+      w->dtrue = w->ones;
+      int st2 = run_cg<float>(h.p32, w, w->v32, w->x32, w->r32, w->p32, w->q32, o->maxit - h.total, chunk,
+                              &w->graph32, &w->graph_chunk32, &ran);
+      w->dtrue = dtrue_saved;
+      ZI_CHECK(st2);
+    } else {
+      ZI_CHECK(run_cg<double>(h.p64, w, w->v64, w->X, w->R, w->P, w->Q, o->maxit - h.total, chunk, &w->graph64,
+                              &w->graph_chunk64, &ran));
+    }
+    ZI_CHECK(head_after_inner(h, ran));
+  }
+  ZI_CHECK(head_finish(h, Tout, iters, relres));
   ZI_CUDA(cudaEventRecord(ev, st));
   ZI_CUDA(cudaStreamWaitEvent(user, ev, 0));
   ZI_CUDA(cudaStreamSynchronize(st));
   cudaEventDestroy(ev);
-  if (iters)
-    for (int c = 0; c < ncol; ++c) iters[c] = h_iters[c];
-  S->has_T = 1;
-  return status;
+  return h.status;
+}
+
+// ---------------------------------------------------------------------------
+// Batched solve: the CG iterations of many heads in one persistent,
+// cooperative launch.  Every head gets its own partition of the resident
+// blocks (sized by its per-iteration work); the blocks of a head meet at
+// per-head barriers, and the last block to arrive at a barrier reduces the
+// column partials (alpha, or beta and the stop tests) before releasing the
+// others.  Barrier waits are bounded: a wait that exceeds its budget sets
+// DEV_ERR_TIMEOUT and the kernel returns.
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct BatchHead {
+  int64_t n;
+  int ld, nv, tpr, cptv, ncol, blk0, nblk, freeze, maxit;
+  const int32_t* rowptr;
+  const int32_t* colind;
+  const T* vals;
+  T *X, *R, *P, *Q;
+  const double* dtrue;
+  double *rho, *alpha, *beta, *stop2;
+  int *conv, *iters, *cnt;
+  double *part0, *part1, *part2;
+  unsigned* bar;  // [0] arrivals, [1] generation
+};
+
+constexpr long long BAR_SPIN_LIMIT = 4000000;  // a few seconds with the back-off below
+
+// Arrive at the head barrier; returns the generation to wait on and whether
+// this block arrived last.
+__device__ __forceinline__ unsigned bar_arrive(unsigned* bar, int nblk, bool* last) {
+  __shared__ unsigned s_gen;
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_gen = atomicAdd(&bar[1], 0u);
+    __threadfence();
+    unsigned a = atomicAdd(&bar[0], 1u);
+    s_last = (a == (unsigned)nblk - 1u);
+  }
+  __syncthreads();
+  *last = s_last != 0;
+  return s_gen;
+}
+__device__ __forceinline__ void bar_release(unsigned* bar) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicExch(&bar[0], 0u);
+    __threadfence();
+    atomicAdd(&bar[1], 1u);
+  }
+  __syncthreads();
+}
+__device__ __forceinline__ bool bar_wait(unsigned* bar, unsigned gen, int* err) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    long long spins = 0;
+    int ok = 1;
+    while (atomicAdd(&bar[1], 0u) == gen) {
+      if (++spins > BAR_SPIN_LIMIT) {
+        atomicOr(err, DEV_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Column totals of this block into part[lb][0..ld) (runtime cptv <= CPTVMAX).
+template <int CPTVMAX, int W, typename AccT>
+__device__ __forceinline__ void batch_block_totals(AccT (&acc)[CPTVMAX][W], int g, int c, int rpb, int tpr, int cptv,
+                                                   int ld, double* sred, double* out) {
+  if (g < rpb) {
+#pragma unroll
+    for (int v = 0; v < CPTVMAX; ++v)
+      if (v < cptv)
+#pragma unroll
+        for (int k = 0; k < W; ++k) sred[g * ld + (c + v * tpr) * W + k] = (double)acc[v][k];
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < ld; col += blockDim.x) {
+    double s = 0.0;
+    for (int gg = 0; gg < rpb; ++gg) s += sred[gg * ld + col];
+    out[col] = s;
+  }
+}
+
+__device__ __forceinline__ double batch_column_sum(const double* __restrict__ part, int nblk, int ld, int col) {
+  double s = 0.0;
+  int b = 0;
+  for (; b + 8 <= nblk; b += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = part[(int64_t)(b + u) * ld + col];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  for (; b < nblk; ++b) s += part[(int64_t)b * ld + col];
+  return s;
+}
+
+template <typename T, int CPTVMAX>
+__global__ void __launch_bounds__(256, 2) k_cg_batched(const BatchHead<T>* __restrict__ heads,
+                                                       const int* __restrict__ block_head, int chunk,
+                                                       int* __restrict__ err) {
+  using V = typename Vec<T>::type;
+  constexpr int W = Vec<T>::W;
+  constexpr int G = sizeof(T) == 8 ? 4 : 8;
+  extern __shared__ double sred[];
+  __shared__ double s_alpha[MAX_LD], s_beta[MAX_LD];
+  __shared__ int s_nact, s_nreach, s_stop;
+  const BatchHead<T> H = heads[block_head[blockIdx.x]];
+  const int lb = blockIdx.x - H.blk0;
+  const int tpr = H.tpr, cptv = H.cptv, nv = H.nv, ld = H.ld;
+  const int rpb = blockDim.x / tpr;
+  const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
+  const RowWalk rw = row_walk_sub(H.n, rpb, g, lb, H.nblk);
+  const V* Pv = reinterpret_cast<const V*>(H.P);
+  V* Qv = reinterpret_cast<V*>(H.Q);
+  V* Rv = reinterpret_cast<V*>(H.R);
+  V* Xv = reinterpret_cast<V*>(H.X);
+  V* Pw = reinterpret_cast<V*>(H.P);
+  for (int it = 0; it < chunk; ++it) {
+    if (threadIdx.x == 0) {
+      const int active = atomicAdd(&H.cnt[0], 0);
+      const int reached = atomicAdd(&H.cnt[2], 0);
+      const int done_it = atomicAdd(&H.cnt[1], 0);
+      s_stop = (active == 0) || (!H.freeze && reached > 0) || done_it >= H.maxit;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    // ---- phase A: Q = A P, p.q partials
+    T acc_pq[CPTVMAX][W];
+#pragma unroll
+    for (int v = 0; v < CPTVMAX; ++v)
+#pragma unroll
+      for (int k = 0; k < W; ++k) acc_pq[v][k] = T(0);
+    for (int64_t i = rw_first(rw); i >= 0; i = rw_next(rw, i)) {
+      V acc[CPTVMAX];
+#pragma unroll
+      for (int v = 0; v < CPTVMAX; ++v) acc[v] = vzero<V>();
+      const int r0 = __ldg(H.rowptr + i), r1 = __ldg(H.rowptr + i + 1);
+      for (int k = r0; k < r1; k += G) {
+        int j[G];
+        T a[G];
+        load_batch<T, G>(k, r1, H.colind, H.vals, j, a);
+        V x[G][CPTVMAX];
+#pragma unroll
+        for (int u = 0; u < G; ++u)
+#pragma unroll
+          for (int v = 0; v < CPTVMAX; ++v)
+            x[u][v] = (j[u] >= 0 && v < cptv) ? ldg_v(Pv + (int64_t)j[u] * nv + c + v * tpr) : vzero<V>();
+#pragma unroll
+        for (int u = 0; u < G; ++u)
+#pragma unroll
+          for (int v = 0; v < CPTVMAX; ++v) vfma(acc[v], a[u], x[u][v]);
+      }
+#pragma unroll
+      for (int v = 0; v < CPTVMAX; ++v) {
+        if (v >= cptv) continue;
+        const int64_t o = i * nv + c + v * tpr;
+        Qv[o] = acc[v];
+        V p = ldg_v(Pv + o);
+#pragma unroll
+        for (int kk = 0; kk < W; ++kk) acc_pq[v][kk] += vget(p, kk) * vget(acc[v], kk);
+      }
+    }
+    batch_block_totals<CPTVMAX, W, T>(acc_pq, g, c, rpb, tpr, cptv, ld, sred, H.part0 + (int64_t)lb * ld);
+    bool last;
+    unsigned gen = bar_arrive(H.bar, H.nblk, &last);
+    if (last) {
+      for (int col = threadIdx.x; col < ld; col += blockDim.x) {
+        double sum = batch_column_sum(H.part0, H.nblk, ld, col);
+        double a = 0.0;
+        if (col < H.ncol && !H.conv[col] && sum > 0.0 && isfinite(sum)) a = H.rho[col] / sum;
+        H.alpha[col] = a;
+      }
+      bar_release(H.bar);
+    } else if (!bar_wait(H.bar, gen, err)) {
+      return;
+    }
+    for (int col = threadIdx.x; col < ld; col += blockDim.x) s_alpha[col] = H.alpha[col];
+    __syncthreads();
+    // ---- phase B: r -= alpha q, r.r and D-weighted r.r partials
+    T rr[CPTVMAX][W], rd[CPTVMAX][W];
+#pragma unroll
+    for (int v = 0; v < CPTVMAX; ++v)
+#pragma unroll
+      for (int k = 0; k < W; ++k) rr[v][k] = rd[v][k] = T(0);
+    for (int64_t i = rw_first(rw); i >= 0; i = rw_next(rw, i)) {
+      const T di = (T)__ldg(H.dtrue + i);
+#pragma unroll
+      for (int v = 0; v < CPTVMAX; ++v) {
+        if (v >= cptv) continue;
+        const int64_t o = i * nv + c + v * tpr;
+        V q = Qv[o], r = Rv[o];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          T rv = vget(r, k) - (T)s_alpha[(c + v * tpr) * W + k] * vget(q, k);
+          vset(r, k, rv);
+          rr[v][k] += rv * rv;
+          rd[v][k] += di * rv * rv;
+        }
+        Rv[o] = r;
+      }
+    }
+    batch_block_totals<CPTVMAX, W, T>(rr, g, c, rpb, tpr, cptv, ld, sred, H.part1 + (int64_t)lb * ld);
+    __syncthreads();
+    batch_block_totals<CPTVMAX, W, T>(rd, g, c, rpb, tpr, cptv, ld, sred, H.part2 + (int64_t)lb * ld);
+    gen = bar_arrive(H.bar, H.nblk, &last);
+    if (last) {
+      if (threadIdx.x == 0) s_nact = s_nreach = 0;
+      __syncthreads();
+      const int itn = H.cnt[1] + 1;
+      for (int col = threadIdx.x; col < ld; col += blockDim.x) {
+        double r2 = batch_column_sum(H.part1, H.nblk, ld, col);
+        double d2 = batch_column_sum(H.part2, H.nblk, ld, col);
+        double be = 0.0;
+        if (col < H.ncol && !H.conv[col]) {
+          const bool hit = d2 <= H.stop2[col];
+          if (!(r2 > 0.0) || (hit && H.freeze)) {
+            H.conv[col] = 1;
+            H.iters[col] = itn;
+          } else {
+            be = r2 / H.rho[col];
+            H.rho[col] = r2;
+            H.iters[col] = itn;
+            atomicAdd(&s_nact, 1);
+            if (hit) atomicAdd(&s_nreach, 1);
+          }
+        }
+        H.beta[col] = be;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        H.cnt[0] = s_nact;
+        H.cnt[1] = itn;
+        H.cnt[2] = s_nreach;
+      }
+      bar_release(H.bar);
+    } else if (!bar_wait(H.bar, gen, err)) {
+      return;
+    }
+    for (int col = threadIdx.x; col < ld; col += blockDim.x) s_beta[col] = H.beta[col];
+    __syncthreads();
+    // ---- phase C: x += alpha p, p = r + beta p
+    for (int64_t i = rw_first(rw); i >= 0; i = rw_next(rw, i)) {
+#pragma unroll
+      for (int v = 0; v < CPTVMAX; ++v) {
+        if (v >= cptv) continue;
+        const int64_t o = i * nv + c + v * tpr;
+        V r = Rv[o], p = Pw[o], x = Xv[o];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          const int col = (c + v * tpr) * W + k;
+          vset(x, k, vget(x, k) + (T)s_alpha[col] * vget(p, k));
+          vset(p, k, vget(r, k) + (T)s_beta[col] * vget(p, k));
+        }
+        Xv[o] = x;
+        Pw[o] = p;
+      }
+    }
+    gen = bar_arrive(H.bar, H.nblk, &last);
+    if (last) {
+      bar_release(H.bar);
+    } else if (!bar_wait(H.bar, gen, err)) {
+      return;
+    }
+  }
+}
+
+constexpr int BATCH_CPTV = 4;
+
+template <typename T>
+static int run_batched_chunk(std::vector<HeadRun*>& act, int chunk, cudaStream_t st, int* d_err) {
+  const void* fn = (const void*)k_cg_batched<T, BATCH_CPTV>;
+  // dynamic shared memory: the largest rpb * ld over the heads
+  size_t smem = 0;
+  for (HeadRun* h : act) {
+    const CgPlan& p = sizeof(T) == 4 ? h->p32 : h->p64;
+    smem = std::max(smem, sizeof(double) * (size_t)(BLOCK / p.tpr) * p.ld);
+  }
+  ZI_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  ZI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BLOCK, smem));
+  if (occ < 1) return set_error(ZI_ERR_ARG, "batched kernel does not fit on an SM");
+  const int G = sm_count() * occ;
+  const int nh = (int)act.size();
+  if (nh > G) return set_error(ZI_ERR_ARG, "more heads (%d) than resident blocks (%d)", nh, G);
+  // blocks per head, proportional to the per-iteration work n * ld (at least one)
+  std::vector<double> wgt(nh);
+  double wsum = 0.0;
+  for (int k = 0; k < nh; ++k) {
+    wgt[k] = (double)act[k]->S->n * (double)act[k]->S->solver->ld;
+    wsum += wgt[k];
+  }
+  std::vector<int> nb(nh, 1);
+  int used = nh;
+  for (int k = 0; k < nh; ++k) {
+    int extra = (int)floor((double)(G - nh) * wgt[k] / wsum);
+    nb[k] += extra;
+    used += extra;
+  }
+  for (int k = 0; used < G; k = (k + 1) % nh, ++used) nb[k] += 1;
+  for (int k = 0; k < nh; ++k) nb[k] = std::min(nb[k], act[k]->S->solver->nblk);
+  std::vector<BatchHead<T>> hh(nh);
+  std::vector<int> bh;
+  int blk = 0;
+  for (int k = 0; k < nh; ++k) {
+    HeadRun* h = act[k];
+    SolverScratch* w = h->S->solver;
+    const CgPlan& p = sizeof(T) == 4 ? h->p32 : h->p64;
+    BatchHead<T>& b = hh[k];
+    b.n = h->S->n;
+    b.ld = w->ld;
+    b.nv = w->ld / Vec<T>::W;
+    b.tpr = p.tpr;
+    b.cptv = p.cptv;
+    b.ncol = h->S->n_rhs;
+    b.blk0 = blk;
+    b.nblk = nb[k];
+    b.freeze = sizeof(T) == 8 ? 1 : 0;
+    b.maxit = h->o->maxit - h->total;
+    if constexpr (sizeof(T) == 4) {
+      b.rowptr = w->rowptr32;
+      b.colind = w->colind32;
+      b.vals = w->v32;
+      b.X = w->x32; b.R = w->r32; b.P = w->p32; b.Q = w->q32;
+      b.dtrue = w->ones;
+    } else {
+      b.rowptr = h->S->rowptr;
+      b.colind = h->S->colind;
+      b.vals = w->v64;
+      b.X = w->X; b.R = w->R; b.P = w->P; b.Q = w->Q;
+      b.dtrue = w->dtrue;
+    }
+    b.rho = w->rho; b.alpha = w->alpha; b.beta = w->beta; b.stop2 = w->stop2;
+    b.conv = w->conv; b.iters = w->iters; b.cnt = w->cnt;
+    b.part0 = w->part0; b.part1 = w->part1; b.part2 = w->part2;
+    b.bar = w->bar;
+    for (int q = 0; q < nb[k]; ++q) bh.push_back(k);
+    blk += nb[k];
+    ZI_CUDA(cudaMemsetAsync(w->bar, 0, 2 * sizeof(unsigned), st));
+  }
+  DevTmp<BatchHead<T>> d_heads;
+  DevTmp<int> d_bh;
+  ZI_CHECK(d_heads.alloc(nh, st));
+  ZI_CHECK(d_bh.alloc(bh.size(), st));
+  ZI_CUDA(cudaMemcpyAsync(d_heads.p, hh.data(), sizeof(BatchHead<T>) * nh, cudaMemcpyHostToDevice, st));
+  ZI_CUDA(cudaMemcpyAsync(d_bh.p, bh.data(), sizeof(int) * bh.size(), cudaMemcpyHostToDevice, st));
+  const BatchHead<T>* a0 = d_heads.p;
+  const int* a1 = d_bh.p;
+  int a2 = chunk;
+  int* a3 = d_err;
+  void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3};
+  ZI_CUDA(cudaLaunchCooperativeKernel(fn, dim3(blk), dim3(BLOCK), args, smem, st));
+  count_launches(1);
+  ZI_CUDA(cudaStreamSynchronize(st));  // host arrays above die with this frame
+  return ZI_OK;
+}
+
+int transfer_batched_impl(zi_system* const* sys, int nb, const zi_solver_opts* o, double* const* Tout,
+                          int32_t* const* iters, cudaStream_t user) {
+  cudaStream_t st;
+  ZI_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t ev;
+  ZI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  ZI_CUDA(cudaEventRecord(ev, user));
+  ZI_CUDA(cudaStreamWaitEvent(st, ev, 0));
+  std::vector<HeadRun> heads(nb);
+  int status = ZI_OK;
+  auto run = [&]() -> int {
+    DevTmp<int> d_err;
+    ZI_CHECK(d_err.alloc(1, st));
+    ZI_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int), st));
+    for (int b = 0; b < nb; ++b) {
+      heads[b].S = sys[b];
+      heads[b].o = o;
+      heads[b].st = st;
+      ZI_CHECK(ensure_scratch(sys[b], o, st));
+      if (!sys[b]->solver->bar) ZI_CHECK(dalloc_n(&sys[b]->solver->bar, 2, st));
+      ZI_CHECK(head_begin(heads[b]));
+    }
+    const int chunk = o->check_every > 0 ? o->check_every : 25;
+    const bool mixed = o->precision == ZI_MIXED;
+    for (;;) {
+      std::vector<HeadRun*> act;
+      for (auto& h : heads)
+        if (!h.done) act.push_back(&h);
+      if (act.empty()) break;
+      if (mixed)
+        ZI_CHECK(run_batched_chunk<float>(act, chunk, st, d_err.p));
+      else
+        ZI_CHECK(run_batched_chunk<double>(act, chunk, st, d_err.p));
+      int herr = 0;
+      ZI_CUDA(cudaMemcpyAsync(&herr, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      ZI_CUDA(cudaStreamSynchronize(st));
+      if (herr) return device_error_to_status(herr);
+      for (HeadRun* h : act) {
+        int c3[3];
+        ZI_CUDA(cudaMemcpyAsync(c3, h->S->solver->cnt, sizeof(c3), cudaMemcpyDeviceToHost, st));
+        ZI_CUDA(cudaStreamSynchronize(st));
+        const bool phase_end = c3[0] == 0 || (mixed && c3[2] > 0) || h->total + c3[1] >= o->maxit;
+        if (phase_end) ZI_CHECK(head_after_inner(*h, c3[1]));
+      }
+    }
+    for (int b = 0; b < nb; ++b) {
+      ZI_CHECK(head_finish(heads[b], Tout ? Tout[b] : nullptr, iters ? iters[b] : nullptr, nullptr));
+      if (heads[b].status != ZI_OK) status = heads[b].status;
+    }
+    return ZI_OK;
+  };
+  int rs = run();
+  cudaEventRecord(ev, st);
+  cudaStreamWaitEvent(user, ev, 0);
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(ev);
+  cudaStreamDestroy(st);
+  return rs != ZI_OK ? rs : status;
 }
 
 }  // namespace zi
@@ -1525,14 +2044,12 @@ extern "C" int zi_transfer_batched(zi_system* const* sys, int nb, const zi_solve
                                    int32_t* const* iters, cudaStream_t s) {
   if (!sys || nb < 1) return set_error(ZI_ERR_ARG, "need at least one system");
   ZI_CHECK(check_opts(o));
-  int worst = ZI_OK;
   for (int b = 0; b < nb; ++b) {
     if (!sys[b]) return set_error(ZI_ERR_ARG, "null system %d", b);
-    int st = transfer_impl(sys[b], o, T ? T[b] : nullptr, iters ? iters[b] : nullptr, nullptr, s);
-    if (st != ZI_OK && st != ZI_ERR_NOT_CONVERGED) return st;
-    if (st != ZI_OK) worst = st;
+    for (int c = 0; c < b; ++c)
+      if (sys[c] == sys[b]) return set_error(ZI_ERR_ARG, "system %d appears twice", b);
   }
-  return worst;
+  return transfer_batched_impl(sys, nb, o, T, iters, s);
 }
 
 namespace zi {

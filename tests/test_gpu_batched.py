@@ -1,0 +1,78 @@
+"""Batched transfer solve: many heads of different sizes and electrode counts
+in one persistent launch, against per-head solves and the oracle."""
+import numpy as np
+import pytest
+
+from oracle import zi_oracle as O
+from paper_1811_07717_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1811_07717_gb300 import zi  # noqa: E402
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+SPECS = [
+    W.three_shell(0.006, 16, 40, seed=31, electrode_radius=0.009),
+    W.three_shell(0.008, 32, 40, seed=32, r_out=0.1, electrode_radius=0.012),
+    W.unit_sphere_point(h=0.2, n_electrodes=12, n_dipoles=30),
+    W.three_shell(0.005, 64, 40, seed=33, r_out=0.085, electrode_radius=0.007),
+]
+
+
+def _build(spec):
+    mesh = zi.mesh_from_grid(spec.h, spec.radii)
+    s6 = W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(),
+                        mesh["labels"].cpu().numpy())
+    centres, z = W.electrode_inputs(spec)
+    pos, _ = W.dipole_inputs(spec)
+    system = zi.System(mesh["nodes"], mesh["tets"], s6, mesh["bfaces"], centres, model=spec.electrode_model,
+                       z=z if spec.electrode_model == "cem" else None, radius=spec.electrode_radius)
+    dip = zi.locate_dipoles_grid(spec.h, spec.radii, pos)
+    return system, dip
+
+
+@pytest.mark.parametrize("precision", [zi.FP64, zi.MIXED], ids=["fp64", "mixed"])
+def test_batched_matches_per_head_solves(precision):
+    opts = zi.SolverOpts(tol=1e-10, precision=precision)
+    built = [_build(sp) for sp in SPECS]
+    systems = [b[0] for b in built]
+    Tb, itb = zi.transfer_batched(systems, opts, want_T=True)
+    for (system, dip), spec, T, it in zip(built, SPECS, Tb, itb):
+        assert np.all(it > 0)
+        single = _build(spec)[0]
+        Ts, its, rr = single.transfer(opts)
+        assert rel(T.cpu().numpy(), Ts.cpu().numpy()) < 1e-8
+        single.close()
+        # the batched T feeds the lead field directly
+        L = system.leadfield(dip).cpu().numpy()
+        Lref, *_ = O.leadfield_from_spec(spec, W)
+        assert rel(L, Lref) < (1e-8 if precision == zi.FP64 else 1e-6)
+        system.close()
+
+
+def test_batched_is_deterministic():
+    opts = zi.SolverOpts(tol=1e-10, precision=zi.MIXED)
+    outs = []
+    for _ in range(2):
+        systems = [_build(sp)[0] for sp in SPECS[:3]]
+        Tb, itb = zi.transfer_batched(systems, opts, want_T=True)
+        outs.append([t.cpu().numpy() for t in Tb])
+        for s in systems:
+            s.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_batched_rejects_duplicates():
+    system, _ = _build(SPECS[2])
+    with pytest.raises(zi.ZiError):
+        zi.transfer_batched([system, system])
+    system.close()
