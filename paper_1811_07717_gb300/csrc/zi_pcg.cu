@@ -1596,6 +1596,11 @@ struct BatchHead {
   const int32_t* rowptr;
   const int32_t* colind;
   const T* vals;
+  const int4* ell_ci;  // FP32 ELL copy (null: CSR)
+  const float4* ell_va;
+  const int32_t* tail_ptr;
+  const int32_t* tail_ci;
+  const float* tail_va;
   T *X, *R, *P, *Q;
   const double* dtrue;
   double *rho, *alpha, *beta, *stop2;
@@ -1604,7 +1609,7 @@ struct BatchHead {
   unsigned* bar;  // [0] arrivals, [1] generation
 };
 
-constexpr long long BAR_SPIN_LIMIT = 4000000;  // a few seconds with the back-off below
+constexpr long long BAR_SPIN_LIMIT = 2000000;  // a few seconds with the back-off below
 
 // Arrive at the head barrier; returns the generation to wait on and whether
 // this block arrived last.
@@ -1643,7 +1648,7 @@ __device__ __forceinline__ bool bar_wait(unsigned* bar, unsigned gen, int* err) 
         ok = 0;
         break;
       }
-      __nanosleep(64);
+      __nanosleep(256);
     }
     __threadfence();
     s_ok = ok;
@@ -1695,7 +1700,11 @@ __global__ void __launch_bounds__(256, 2) k_cg_batched(const BatchHead<T>* __res
   extern __shared__ double sred[];
   __shared__ double s_alpha[MAX_LD], s_beta[MAX_LD];
   __shared__ int s_nact, s_nreach, s_stop;
-  const BatchHead<T> H = heads[block_head[blockIdx.x]];
+  // the head's descriptor in shared memory, not in registers
+  __shared__ BatchHead<T> sH;
+  if (threadIdx.x == 0) sH = heads[block_head[blockIdx.x]];
+  __syncthreads();
+  const BatchHead<T>& H = sH;
   const int lb = blockIdx.x - H.blk0;
   const int tpr = H.tpr, cptv = H.cptv, nv = H.nv, ld = H.ld;
   const int rpb = blockDim.x / tpr;
@@ -1721,34 +1730,79 @@ __global__ void __launch_bounds__(256, 2) k_cg_batched(const BatchHead<T>* __res
     for (int v = 0; v < CPTVMAX; ++v)
 #pragma unroll
       for (int k = 0; k < W; ++k) acc_pq[v][k] = T(0);
-    for (int64_t i = rw_first(rw); i >= 0; i = rw_next(rw, i)) {
-      V acc[CPTVMAX];
+    if constexpr (sizeof(T) == 4) {
+      if (H.ell_ci) {
+        // ELL rows: next row's column indices prefetched behind the gathers
+        int64_t i = rw_first(rw);
+        int jn[ELL_K];
+        if (i >= 0) ell_cols(H.ell_ci, i, jn);
+        while (i >= 0) {
+          int j[ELL_K];
 #pragma unroll
-      for (int v = 0; v < CPTVMAX; ++v) acc[v] = vzero<V>();
-      const int r0 = __ldg(H.rowptr + i), r1 = __ldg(H.rowptr + i + 1);
-      for (int k = r0; k < r1; k += G) {
-        int j[G];
-        T a[G];
-        load_batch<T, G>(k, r1, H.colind, H.vals, j, a);
-        V x[G][CPTVMAX];
+          for (int u = 0; u < ELL_K; ++u) j[u] = jn[u];
+          const bool tail = j[0] < 0;
+          j[0] = tail ? ~j[0] : j[0];
+          V x[ELL_K][CPTVMAX];
 #pragma unroll
-        for (int u = 0; u < G; ++u)
+          for (int u = 0; u < ELL_K; ++u)
 #pragma unroll
-          for (int v = 0; v < CPTVMAX; ++v)
-            x[u][v] = (j[u] >= 0 && v < cptv) ? ldg_v(Pv + (int64_t)j[u] * nv + c + v * tpr) : vzero<V>();
+            for (int v = 0; v < CPTVMAX; ++v)
+              x[u][v] = (j[u] >= 0 && v < cptv) ? ldg_v(Pv + (j[u] * nv + c + v * tpr)) : vzero<V>();
+          const float4 a0 = __ldg(H.ell_va + i * (ELL_K / 4)), a1 = __ldg(H.ell_va + i * (ELL_K / 4) + 1);
+          const int64_t inext = rw_next(rw, i);
+          if (inext >= 0) ell_cols(H.ell_ci, inext, jn);
+          const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
 #pragma unroll
-        for (int u = 0; u < G; ++u)
+          for (int v = 0; v < CPTVMAX; ++v) {
+            if (v >= cptv) continue;
+            V acc = vzero<V>();
 #pragma unroll
-          for (int v = 0; v < CPTVMAX; ++v) vfma(acc[v], a[u], x[u][v]);
+            for (int u = 0; u < ELL_K; ++u) vfma(acc, a[u], x[u][v]);
+            if (tail) {
+              const int t0 = __ldg(H.tail_ptr + i), t1 = __ldg(H.tail_ptr + i + 1);
+              for (int t = t0; t < t1; ++t)
+                vfma(acc, __ldg(H.tail_va + t), ldg_v(Pv + (__ldg(H.tail_ci + t) * nv + c + v * tpr)));
+            }
+            Qv[i * nv + c + v * tpr] = acc;
+#pragma unroll
+            for (int kk = 0; kk < W; ++kk) acc_pq[v][kk] += vget(x[0][v], kk) * vget(acc, kk);
+          }
+          i = inext;
+        }
       }
+    }
+    if (sizeof(T) == 8 || !H.ell_ci) {
+      for (int64_t i = rw_first(rw); i >= 0; i = rw_next(rw, i)) {
+        V acc[CPTVMAX];
 #pragma unroll
-      for (int v = 0; v < CPTVMAX; ++v) {
-        if (v >= cptv) continue;
-        const int64_t o = i * nv + c + v * tpr;
-        Qv[o] = acc[v];
-        V p = ldg_v(Pv + o);
+        for (int v = 0; v < CPTVMAX; ++v) acc[v] = vzero<V>();
+        const int r0 = __ldg(H.rowptr + i), r1 = __ldg(H.rowptr + i + 1);
+        for (int k = r0; k < r1; k += G) {
+          int j[G];
+          T a[G];
+          load_batch<T, G>(k, r1, H.colind, H.vals, j, a);
+          V x[G][CPTVMAX];
 #pragma unroll
-        for (int kk = 0; kk < W; ++kk) acc_pq[v][kk] += vget(p, kk) * vget(acc[v], kk);
+          for (int u = 0; u < G; ++u)
+#pragma unroll
+            for (int v = 0; v < CPTVMAX; ++v)
+              x[u][v] = (j[u] >= 0 && v < cptv) ? ldg_v(Pv + (int64_t)j[u] * nv + c + v * tpr) : vzero<V>();
+#pragma unroll
+          for (int v = 0; v < CPTVMAX; ++v) {
+            if (v >= cptv) continue;
+#pragma unroll
+            for (int u = 0; u < G; ++u) vfma(acc[v], a[u], x[u][v]);
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < CPTVMAX; ++v) {
+          if (v >= cptv) continue;
+          const int64_t o = i * nv + c + v * tpr;
+          Qv[o] = acc[v];
+          V p = ldg_v(Pv + o);
+#pragma unroll
+          for (int kk = 0; kk < W; ++kk) acc_pq[v][kk] += vget(p, kk) * vget(acc[v], kk);
+        }
       }
     }
     batch_block_totals<CPTVMAX, W, T>(acc_pq, g, c, rpb, tpr, cptv, ld, sred, H.part0 + (int64_t)lb * ld);
@@ -1855,11 +1909,12 @@ __global__ void __launch_bounds__(256, 2) k_cg_batched(const BatchHead<T>* __res
   }
 }
 
-constexpr int BATCH_CPTV = 4;
+// widest row split of a head (ld <= 256): FP32 2 vectors per thread, FP64 4
+template <typename T> struct BatchCptv { static constexpr int v = sizeof(T) == 4 ? 2 : 4; };
 
 template <typename T>
 static int run_batched_chunk(std::vector<HeadRun*>& act, int chunk, cudaStream_t st, int* d_err) {
-  const void* fn = (const void*)k_cg_batched<T, BATCH_CPTV>;
+  const void* fn = (const void*)k_cg_batched<T, BatchCptv<T>::v>;
   // dynamic shared memory: the largest rpb * ld over the heads
   size_t smem = 0;
   for (HeadRun* h : act) {
@@ -1907,10 +1962,20 @@ static int run_batched_chunk(std::vector<HeadRun*>& act, int chunk, cudaStream_t
     b.nblk = nb[k];
     b.freeze = sizeof(T) == 8 ? 1 : 0;
     b.maxit = h->o->maxit - h->total;
+    b.ell_ci = nullptr;
+    b.ell_va = nullptr;
+    b.tail_ptr = nullptr;
+    b.tail_ci = nullptr;
+    b.tail_va = nullptr;
     if constexpr (sizeof(T) == 4) {
       b.rowptr = w->rowptr32;
       b.colind = w->colind32;
       b.vals = w->v32;
+      b.ell_ci = reinterpret_cast<const int4*>(w->ell_ci);
+      b.ell_va = reinterpret_cast<const float4*>(w->ell_va);
+      b.tail_ptr = w->tail_ptr;
+      b.tail_ci = w->tail_ci;
+      b.tail_va = w->tail_va;
       b.X = w->x32; b.R = w->r32; b.P = w->p32; b.Q = w->q32;
       b.dtrue = w->ones;
     } else {
