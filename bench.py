@@ -39,7 +39,7 @@ WORKLOAD = "three-shell sphere 80/86/92 mm, h=2 mm Kuhn grid (428185 nodes, 2447
            "128 CEM electrodes r=5 mm z=2e-3 Ohm m^2, 20000 dipoles x 3, PCG tol 1e-10"
 # ncu DRAM traffic per launch of the FP32 SpMM on this workload, from the capture
 # summarised in profiles/ (None until taken, or once the kernel source changed).
-SPMM_TRAFFIC = {"source_sha": None, "bytes": None}
+SPMM_TRAFFIC = {"source_sha": "235baaeef3bf0864", "bytes": 247.799552e6 + 188.901120e6}
 
 
 def parse():
@@ -265,7 +265,7 @@ def main():
     peak, peak_note = measured_peak_gbs()
     achieved = bytes32 / (ms32 * 1e-3) / 1e9
     traffic = SPMM_TRAFFIC["bytes"] if SPMM_TRAFFIC["source_sha"] == spmm_source_sha() else None
-    roofline = {"bound": "hbm", "kernel": "k_spmm_dot<float> (FP32 SpMM fused with column dots)",
+    roofline = {"bound": "hbm", "kernel": "k_spmm_ell<1> (FP32 ELL SpMM fused with the p.q column dots)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_note": peak_note, "traffic": traffic, "algorithmic_bytes": bytes32,
                 "ms_per_launch": ms32}
