@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison build")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--h", type=float, default=0.002, help="grid step (m) of the timed workload")
+    ap.add_argument("--workload", default="shell2mm", choices=["shell2mm", "aniso1mm", "batch"],
+                    help="shell2mm: the headline workload; aniso1mm: 1 mm anisotropic-skull head, 256 "
+                         "electrodes, 100k dipoles; batch: 24 heads, batched vs per-head solves")
     return ap.parse_args()
 
 
@@ -173,6 +175,51 @@ def spmm_source_sha():
 
 
 # ---------------------------------------------------------------------------
+# batched workload: 24 heads, one persistent launch vs per-head solves
+# ---------------------------------------------------------------------------
+
+def batch_workload(args):
+    import torch
+    from paper_1811_07717_gb300 import workloads as W
+    from paper_1811_07717_gb300 import _build, zi
+    _build.build()
+    heads = W.config_batch()
+    systems = []
+    for spec in heads:
+        mesh = zi.mesh_from_grid(spec.h, spec.radii)
+        s6 = W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(),
+                            mesh["labels"].cpu().numpy())
+        centres, z = W.electrode_inputs(spec)
+        systems.append(zi.System(mesh["nodes"], mesh["tets"], s6, mesh["bfaces"], centres, model="cem", z=z,
+                                 radius=spec.electrode_radius))
+    out = {}
+    for name, prec in (("mixed", zi.MIXED), ("fp64", zi.FP64)):
+        opts = zi.SolverOpts(tol=1e-10, precision=prec)
+        zi.transfer_batched(systems, opts)  # warm-up (allocations, graphs)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record()
+        for s in systems:
+            s.transfer(opts, want_T=False)
+        t1.record()
+        torch.cuda.synchronize()
+        seq = t0.elapsed_time(t1) / 1e3
+        t0.record()
+        zi.transfer_batched(systems, opts)
+        t1.record()
+        torch.cuda.synchronize()
+        out[name] = {"sequential_s": seq, "batched_s": t0.elapsed_time(t1) / 1e3}
+    n = sum(s.info()["n"] for s in systems)
+    line = {"metric": "transfer solve s for 24 heads (batched persistent launch vs per-head launches)",
+            "value": out["mixed"]["batched_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": False, "dtype": "f32 inner PCG / f64 refinement", "data": "synthetic",
+            "config": {"workload": "24 seeded three-shell heads, R 80-100 mm, h in {1.5, 2, 3} mm, "
+                                   "32-256 CEM electrodes", "n_nodes_total": n, "tol": 1e-10},
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -194,7 +241,13 @@ def main():
     from paper_1811_07717_gb300 import _build, zi
     _build.build()
 
-    spec = W.three_shell(args.h, 128, 20000, seed=2)
+    if args.workload == "batch":
+        return batch_workload(args)
+    spec = W.config_three_shell_2mm() if args.workload == "shell2mm" else W.config_three_shell_1mm_aniso()
+    workload = WORKLOAD if args.workload == "shell2mm" else (
+        "three-shell sphere 80/86/92 mm, h=1 mm Kuhn grid (3342701 nodes, 19573872 tets), transversely "
+        "anisotropic skull (radial 0.00132, tangential 0.0132 S/m), 256 CEM electrodes, 100000 dipoles x 3, "
+        "PCG tol 1e-10")
     dev = torch.device("cuda", local)
     mesh = zi.mesh_from_grid(spec.h, spec.radii)
     s6 = W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(), mesh["labels"].cpu().numpy())
@@ -264,7 +317,8 @@ def main():
     system.close()
     peak, peak_note = measured_peak_gbs()
     achieved = bytes32 / (ms32 * 1e-3) / 1e9
-    traffic = SPMM_TRAFFIC["bytes"] if SPMM_TRAFFIC["source_sha"] == spmm_source_sha() else None
+    traffic = (SPMM_TRAFFIC["bytes"] if SPMM_TRAFFIC["source_sha"] == spmm_source_sha()
+               and args.workload == "shell2mm" else None)
     roofline = {"bound": "hbm", "kernel": "k_spmm_ell<1> (FP32 ELL SpMM fused with the p.q column dots)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_note": peak_note, "traffic": traffic, "algorithmic_bytes": bytes32,
@@ -295,7 +349,7 @@ def main():
                "d2h_bytes_per_step": int(Lh.numel() * Lh.element_size())}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and args.workload == "shell2mm":
         try:
             cpu_s = oracle_once()
             cpu = {"value": cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE_TEXT}
@@ -307,8 +361,9 @@ def main():
                 "warmup": args.warmup, "ms_per_step": sec_mixed * 1e3, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner PCG / f64 refinement, assembly, LF",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_nodes": int(d["nodes"].shape[0]),
-                           "n_tets": int(d["tets"].shape[0]), "electrodes": 128, "dipoles": 20000,
+                "config": {"workload": workload, "n_nodes": int(d["nodes"].shape[0]),
+                           "n_tets": int(d["tets"].shape[0]), "electrodes": spec.n_electrodes,
+                           "dipoles": spec.n_dipoles,
                            "precision": "mixed", "l2": "inputs larger than L2 (T alone is 438 MB)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "iterations_mixed_max": int(it_mixed.max()), "relres_mixed_max": float(rr_mixed.max()),

@@ -139,6 +139,19 @@ __device__ __forceinline__ int64_t rw_next(const RowWalk& w, int64_t i) {
   return nx < w.n ? nx : -1;
 }
 
+// Early exit inside a replayed chunk of iterations: once no column is active
+// (FP64) or a column has reached its phase target (mixed phases), the
+// remaining kernels of the chunk return at once.  cnt: [0] active columns,
+// [1] iterations, [2] columns past the phase target, [3] "skip the direction
+// update" -- set by the first SpMM that finds the run stopped, so the
+// direction update of the iteration that stopped the run still happens once.
+__device__ __forceinline__ bool run_stopped(const int* cnt, int freeze) {
+  if (!cnt) return false;
+  const int active = *(volatile const int*)cnt;
+  const int reached = *(volatile const int*)(cnt + 2);
+  return active == 0 || (!freeze && reached > 0);
+}
+
 // Column indices and values of one batch of up to G nonzeros starting at k0
 // (padding: column -1, value 0).
 template <typename T, int G>
@@ -180,7 +193,11 @@ template <typename T, int CPTV>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
     k_spmm_dot(int64_t n, int tpr, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                const T* __restrict__ vals, const T* __restrict__ P, T* __restrict__ Q, int ld,
-               double* __restrict__ partial) {
+               double* __restrict__ partial, int* __restrict__ cnt, int freeze) {
+  if (run_stopped(cnt, freeze)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[3] = 1;
+    return;
+  }
   using V = typename Vec<T>::type;
   constexpr int W = Vec<T>::W;
   constexpr int G = (sizeof(T) == 8 && CPTV > 1) ? 4 : 8;
@@ -272,7 +289,11 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
     k_spmm_ell(int64_t n, int tpr, const int4* __restrict__ ci, const float4* __restrict__ va,
                const int32_t* __restrict__ tail_ptr, const int32_t* __restrict__ tail_ci,
                const float* __restrict__ tail_va, const float* __restrict__ P, float* __restrict__ Q, int ld,
-               double* __restrict__ partial) {
+               double* __restrict__ partial, int* __restrict__ cnt, int freeze) {
+  if (run_stopped(cnt, freeze)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[3] = 1;
+    return;
+  }
   using V = float4;
   constexpr int W = 4;
   extern __shared__ double sred[];
@@ -343,7 +364,8 @@ template <typename T, int CPTV>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
     k_cg_resid(int64_t n, int tpr, int ld, const double* __restrict__ alpha, const T* __restrict__ Q,
                T* __restrict__ R, const double* __restrict__ dtrue, double* __restrict__ part_rr,
-               double* __restrict__ part_rd) {
+               double* __restrict__ part_rd, const int* __restrict__ cnt, int freeze) {
+  if (run_stopped(cnt, freeze)) return;
   using V = typename Vec<T>::type;
   constexpr int W = Vec<T>::W;
   extern __shared__ double sred[];
@@ -392,7 +414,8 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
 template <typename T, int CPTV>
 __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, int tpr, int ld, const double* __restrict__ alpha,
                                                 const double* __restrict__ beta, const T* __restrict__ R,
-                                                T* __restrict__ P, T* __restrict__ X) {
+                                                T* __restrict__ P, T* __restrict__ X, const int* __restrict__ cnt) {
+  if (cnt && *(volatile const int*)(cnt + 3)) return;
   using V = typename Vec<T>::type;
   constexpr int W = Vec<T>::W;
   const int nv = ld / W;
@@ -475,6 +498,7 @@ __device__ double column_total(const double* __restrict__ part, int nblk, int ld
 
 __global__ void __launch_bounds__(FIN_THREADS) k_fin_alpha(int nblk, int ld, int ncol, const double* __restrict__ part,
                                                            ColState cs) {
+  if (run_stopped(cs.active, cs.freeze)) return;
   __shared__ double sm[FIN_THREADS];
   double s = column_total(part, nblk, ld, sm);
   const int c = threadIdx.x;
@@ -487,6 +511,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin_alpha(int nblk, int ld, int
 
 __global__ void __launch_bounds__(FIN_THREADS) k_fin_beta(int nblk, int ld, int ncol, const double* __restrict__ prr,
                                                           const double* __restrict__ prd, ColState cs) {
+  if (run_stopped(cs.active, cs.freeze)) return;
   __shared__ double sm[FIN_THREADS];
   __shared__ int nact, nreach;
   if (threadIdx.x == 0) nact = nreach = 0;
@@ -895,12 +920,13 @@ int blocks_per_sm_for(int tpr) {
 
 template <typename T>
 int launch_spmm(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, const int32_t* rp,
-                const int32_t* ci, const T* v, const T* P, T* Q, int ld, double* part) {
+                const int32_t* ci, const T* v, const T* P, T* Q, int ld, double* part, int* cnt = nullptr,
+                int freeze = 1) {
   switch (cptv) {
-    case 1: k_spmm_dot<T, 1><<<grid, BLOCK, smem, st>>>(n, tpr, rp, ci, v, P, Q, ld, part); break;
-    case 2: k_spmm_dot<T, 2><<<grid, BLOCK, smem, st>>>(n, tpr, rp, ci, v, P, Q, ld, part); break;
-    case 4: k_spmm_dot<T, 4><<<grid, BLOCK, smem, st>>>(n, tpr, rp, ci, v, P, Q, ld, part); break;
-    case 8: k_spmm_dot<T, 8><<<grid, BLOCK, smem, st>>>(n, tpr, rp, ci, v, P, Q, ld, part); break;
+    case 1: k_spmm_dot<T, 1><<<grid, BLOCK, smem, st>>>(n, tpr, rp, ci, v, P, Q, ld, part, cnt, freeze); break;
+    case 2: k_spmm_dot<T, 2><<<grid, BLOCK, smem, st>>>(n, tpr, rp, ci, v, P, Q, ld, part, cnt, freeze); break;
+    case 4: k_spmm_dot<T, 4><<<grid, BLOCK, smem, st>>>(n, tpr, rp, ci, v, P, Q, ld, part, cnt, freeze); break;
+    case 8: k_spmm_dot<T, 8><<<grid, BLOCK, smem, st>>>(n, tpr, rp, ci, v, P, Q, ld, part, cnt, freeze); break;
     default: return set_error(ZI_ERR_ARG, "unsupported column layout");
   }
   ZI_LAUNCH_CHECK();
@@ -909,13 +935,13 @@ int launch_spmm(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int6
 
 int launch_spmm_ell(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, const int32_t* ci,
                     const float* va, const int32_t* tptr, const int32_t* tci, const float* tva, const float* P,
-                    float* Q, int ld, double* part) {
+                    float* Q, int ld, double* part, int* cnt = nullptr, int freeze = 1) {
   const int4* c4 = reinterpret_cast<const int4*>(ci);
   const float4* v4 = reinterpret_cast<const float4*>(va);
   switch (cptv) {
-    case 1: k_spmm_ell<1><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part); break;
-    case 2: k_spmm_ell<2><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part); break;
-    case 4: k_spmm_ell<4><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part); break;
+    case 1: k_spmm_ell<1><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part, cnt, freeze); break;
+    case 2: k_spmm_ell<2><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part, cnt, freeze); break;
+    case 4: k_spmm_ell<4><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part, cnt, freeze); break;
     default: return set_error(ZI_ERR_ARG, "unsupported column layout");
   }
   ZI_LAUNCH_CHECK();
@@ -924,12 +950,13 @@ int launch_spmm_ell(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, 
 
 template <typename T>
 int launch_resid(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, int ld,
-                 const double* alpha, const T* Q, T* R, const double* dtrue, double* prr, double* prd) {
+                 const double* alpha, const T* Q, T* R, const double* dtrue, double* prr, double* prd,
+                 const int* cnt, int freeze) {
   switch (cptv) {
-    case 1: k_cg_resid<T, 1><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd); break;
-    case 2: k_cg_resid<T, 2><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd); break;
-    case 4: k_cg_resid<T, 4><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd); break;
-    case 8: k_cg_resid<T, 8><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd); break;
+    case 1: k_cg_resid<T, 1><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd, cnt, freeze); break;
+    case 2: k_cg_resid<T, 2><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd, cnt, freeze); break;
+    case 4: k_cg_resid<T, 4><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd, cnt, freeze); break;
+    case 8: k_cg_resid<T, 8><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd, cnt, freeze); break;
     default: return set_error(ZI_ERR_ARG, "unsupported column layout");
   }
   ZI_LAUNCH_CHECK();
@@ -938,12 +965,12 @@ int launch_resid(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int
 
 template <typename T>
 int launch_dir(int cptv, dim3 grid, int tpr, cudaStream_t st, int64_t n, int ld, const double* alpha,
-               const double* beta, const T* R, T* P, T* X) {
+               const double* beta, const T* R, T* P, T* X, const int* cnt) {
   switch (cptv) {
-    case 1: k_cg_dir<T, 1><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X); break;
-    case 2: k_cg_dir<T, 2><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X); break;
-    case 4: k_cg_dir<T, 4><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X); break;
-    case 8: k_cg_dir<T, 8><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X); break;
+    case 1: k_cg_dir<T, 1><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X, cnt); break;
+    case 2: k_cg_dir<T, 2><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X, cnt); break;
+    case 4: k_cg_dir<T, 4><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X, cnt); break;
+    case 8: k_cg_dir<T, 8><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X, cnt); break;
     default: return set_error(ZI_ERR_ARG, "unsupported column layout");
   }
   ZI_LAUNCH_CHECK();
@@ -1061,13 +1088,15 @@ static void size_grids(CgPlan& p) {
 
 // The SpMM of one CG iteration: ELL for the FP32 matrix when available.
 template <typename T>
-static int plan_spmm(const CgPlan& p, const T* vals, const T* P, T* Q, double* part, cudaStream_t st) {
+static int plan_spmm(const CgPlan& p, const T* vals, const T* P, T* Q, double* part, cudaStream_t st,
+                     int* cnt = nullptr, int freeze = 1) {
   if constexpr (sizeof(T) == 4) {
     if (p.ell_ci && p.cptv <= 4)
       return launch_spmm_ell(p.cptv, dim3(p.g_spmm), p.tpr, p.smem, st, p.n, p.ell_ci, p.ell_va, p.tail_ptr,
-                             p.tail_ci, p.tail_va, P, Q, p.ld, part);
+                             p.tail_ci, p.tail_va, P, Q, p.ld, part, cnt, freeze);
   }
-  return launch_spmm<T>(p.cptv, dim3(p.g_spmm), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, vals, P, Q, p.ld, part);
+  return launch_spmm<T>(p.cptv, dim3(p.g_spmm), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, vals, P, Q, p.ld, part,
+                        cnt, freeze);
 }
 
 static CgPlan make_plan(zi_system* S, SolverScratch* w, int cptv, int vecw) {
@@ -1094,14 +1123,14 @@ static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T
   // partials per reduction: one per cluster of each kernel's resident grid
   const int ncl_spmm = p.g_spmm / CLUSTER, ncl_resid = p.g_resid / CLUSTER;
   for (int k = 0; k < chunk; ++k) {
-    ZI_CHECK(plan_spmm<T>(p, vals, P, Q, w->part0, st));
+    ZI_CHECK(plan_spmm<T>(p, vals, P, Q, w->part0, st, w->cnt, cs.freeze));
     k_fin_alpha<<<1, FIN_THREADS, 0, st>>>(ncl_spmm, p.ld, p.ncol, w->part0, cs);
     ZI_LAUNCH_CHECK();
     ZI_CHECK(launch_resid<T>(p.cptv, dim3(p.g_resid), p.tpr, p.smem, st, p.n, p.ld, w->alpha, Q, R, w->dtrue,
-                             w->part1, w->part2));
+                             w->part1, w->part2, w->cnt, cs.freeze));
     k_fin_beta<<<1, FIN_THREADS, 0, st>>>(ncl_resid, p.ld, p.ncol, w->part1, w->part2, cs);
     ZI_LAUNCH_CHECK();
-    ZI_CHECK(launch_dir<T>(p.cptv, dim3(p.g_dir), p.tpr, st, p.n, p.ld, w->alpha, w->beta, R, P, X));
+    ZI_CHECK(launch_dir<T>(p.cptv, dim3(p.g_dir), p.tpr, st, p.n, p.ld, w->alpha, w->beta, R, P, X, w->cnt));
   }
   return ZI_OK;
 }
@@ -1149,7 +1178,7 @@ static int run_cg(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, 
     ZI_CUDA(cudaStreamSynchronize(w->stream));
     if (hcnt[0] == 0 || hcnt[2] > 0) break;
   }
-  *ran = done;
+  *ran = hcnt[1];  // iterations that ran; the rest of the last chunk returned at once
   return ZI_OK;
 }
 
@@ -1192,7 +1221,7 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
     ZI_CHECK(dalloc_n(&w->vec, ld, s));
     ZI_CHECK(dalloc_n(&w->conv, ld, s));
     ZI_CHECK(dalloc_n(&w->iters, ld, s));
-    ZI_CHECK(dalloc_n(&w->cnt, 3, s));
+    ZI_CHECK(dalloc_n(&w->cnt, 4, s));
     ZI_CHECK(dalloc_n(&w->gamma, ld, s));
     ZI_CHECK(dalloc_n(&w->gamma_prev, ld, s));
     ZI_CHECK(dalloc_n(&w->flag, ld, s));
@@ -1242,6 +1271,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_init_cols(int nblk, int ld, int
     cnt[0] = nact;
     cnt[1] = 0;
     cnt[2] = 0;
+    cnt[3] = 0;
   }
 }
 
