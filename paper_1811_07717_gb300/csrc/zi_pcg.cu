@@ -20,6 +20,7 @@
 //  * ZI_MIXED: FP32 matrix and vectors in the inner CG (half the bytes), an
 //    FP64 outer loop  r = b - A x,  x += correction  (iterative refinement).
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -1720,10 +1721,13 @@ __device__ __forceinline__ double batch_column_sum(const double* __restrict__ pa
   return s;
 }
 
+// skip_block >= 0 (fault-injection test only): that block leaves before its
+// first barrier, as a failed block would; the other blocks of its head wait
+// out their bound, set DEV_ERR_TIMEOUT and return.
 template <typename T, int CPTVMAX>
 __global__ void __launch_bounds__(256, 2) k_cg_batched(const BatchHead<T>* __restrict__ heads,
                                                        const int* __restrict__ block_head, int chunk,
-                                                       int* __restrict__ err) {
+                                                       int* __restrict__ err, int skip_block) {
   using V = typename Vec<T>::type;
   constexpr int W = Vec<T>::W;
   constexpr int G = sizeof(T) == 8 ? 4 : 8;
@@ -1837,6 +1841,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_batched(const BatchHead<T>* __res
     }
     batch_block_totals<CPTVMAX, W, T>(acc_pq, g, c, rpb, tpr, cptv, ld, sred, H.part0 + (int64_t)lb * ld);
     bool last;
+    if (it == 0 && (int)blockIdx.x == skip_block) return;  // injected fault: this block leaves
     unsigned gen = bar_arrive(H.bar, H.nblk, &last);
     if (last) {
       for (int col = threadIdx.x; col < ld; col += blockDim.x) {
@@ -2033,7 +2038,10 @@ static int run_batched_chunk(std::vector<HeadRun*>& act, int chunk, cudaStream_t
   const int* a1 = d_bh.p;
   int a2 = chunk;
   int* a3 = d_err;
-  void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3};
+  // test-only fault injection (ZI_TEST_BARRIER_SKIP=1): block 0 leaves before its first barrier
+  const char* fe = getenv("ZI_TEST_BARRIER_SKIP");
+  int a4 = (fe && fe[0] == '1') ? 0 : -1;
+  void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3, (void*)&a4};
   ZI_CUDA(cudaLaunchCooperativeKernel(fn, dim3(blk), dim3(BLOCK), args, smem, st));
   count_launches(1);
   ZI_CUDA(cudaStreamSynchronize(st));  // host arrays above die with this frame

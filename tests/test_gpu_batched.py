@@ -76,3 +76,24 @@ def test_batched_rejects_duplicates():
     with pytest.raises(zi.ZiError):
         zi.transfer_batched([system, system])
     system.close()
+
+
+def test_barrier_timeout_is_reported_and_context_survives(monkeypatch):
+    """Failure detection of the persistent launch: one block leaves before its
+    first barrier (test-only injection), the other blocks of its head give up
+    after their bounded wait and the call returns ZI_ERR_TIMEOUT; the GPU
+    context stays usable and the next solve is correct."""
+    built = [_build(sp) for sp in SPECS[:2]]
+    systems = [b[0] for b in built]
+    opts = zi.SolverOpts(tol=1e-10, precision=zi.FP64)
+    monkeypatch.setenv("ZI_TEST_BARRIER_SKIP", "1")
+    with pytest.raises(zi.ZiError) as e:
+        zi.transfer_batched(systems, opts)
+    assert e.value.status == zi.ZI_ERR_TIMEOUT
+    monkeypatch.delenv("ZI_TEST_BARRIER_SKIP")
+    Tb, itb = zi.transfer_batched(systems, opts, want_T=True)
+    single = _build(SPECS[0])[0]
+    Ts, _, _ = single.transfer(opts)
+    assert rel(Tb[0].cpu().numpy(), Ts.cpu().numpy()) < 1e-8
+    for s in systems + [single]:
+        s.close()
