@@ -61,6 +61,17 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The job's time is the slowest rank's: max of `value` over the process
+    group (identity without one)."""
+    if dist is None or not dist.is_initialized():
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle sample (the baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
@@ -284,11 +295,7 @@ def main():
             t1.record()
             barrier()
         launches = zi.kernel_launches() - l0
-        sec = t0.elapsed_time(t1) / 1e3 / steps
-        if dist is not None:
-            tt = torch.tensor([sec], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            sec = float(tt.item())
+        sec = max_over_ranks(t0.elapsed_time(t1) / 1e3 / steps, dist, dev)
         return sec, L, launches, clk.summary()
 
     mixed = zi.SolverOpts(tol=1e-10, precision=zi.MIXED)
