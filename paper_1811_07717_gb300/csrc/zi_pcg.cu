@@ -125,9 +125,6 @@ struct RowWalk {
 __device__ __forceinline__ RowWalk row_walk(int64_t n, int rpb, int g) {
   return RowWalk{n, 4 * rpb, rpb, g, (int)blockIdx.x, (int)gridDim.x};
 }
-__device__ __forceinline__ RowWalk row_walk_sub(int64_t n, int rpb, int g, int blk, int nblk) {
-  return RowWalk{n, 4 * rpb, rpb, g, blk, nblk};
-}
 __device__ __forceinline__ int64_t rw_first(const RowWalk& w) {
   int64_t i = (int64_t)w.blk * w.C + w.g;
   return (w.g < w.rpb && i < w.n) ? i : -1;
@@ -325,7 +322,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
     for (int u = 0; u < ELL_K; ++u)
 #pragma unroll
       for (int v = 0; v < CPTV; ++v)
-        x[u][v] = j[u] >= 0 ? ldg_v(Pv + (j[u] * nv + v * tpr)) : vzero<V>();  // n*ld/4 < 2^31 (host-checked)
+        x[u][v] = j[u] >= 0 ? ldg_v(Pv + (j[u] * nv + v * tpr)) : vzero<V>();  // n*ld/2 < 2^31 (host-checked)
     const float4 a0 = __ldg(va + i * (ELL_K / 4)), a1 = __ldg(va + i * (ELL_K / 4) + 1);
     const int64_t inext = rw_next(rw, i);
     const bool more = inext >= 0;
@@ -861,7 +858,8 @@ struct SolverScratch {
   int *conv = nullptr, *iters = nullptr, *cnt = nullptr;  // cnt[0] active, cnt[1] iteration, cnt[2] reached
   double *gamma = nullptr, *gamma_prev = nullptr;  // mixed: column scale of the FP32 phase
   int *flag = nullptr, *nact = nullptr;            // mixed: columns within tol / count
-  unsigned* bar = nullptr;                         // batched: per-head barrier (arrivals, generation)
+  unsigned* bar = nullptr;    // batched: [0] arrivals, [1] generation, [2..] group arrivals
+  double* gpart = nullptr;    // batched: group column sums, 3 x ngroups x ld
   bool values_ready = false;   // s, dtrue, v64 match the system's values
   bool v32_ready = false;      // v32 matches
   cudaStream_t stream = nullptr;
@@ -882,7 +880,7 @@ void solver_scratch_free(zi_system* S) {
   cudaStream_t s = 0;
   void* ptrs[] = {w->s, w->dtrue, w->ones, w->v64, w->v32, w->rowptr32, w->colind32, w->ell_ci, w->ell_va, w->tail_ptr, w->tail_ci, w->tail_va, w->X, w->R, w->P, w->Q, w->x32, w->r32, w->p32, w->q32,
                   w->part0, w->part1, w->part2, w->rho, w->alpha, w->beta, w->stop2, w->bb, w->vec,
-                  w->conv, w->iters, w->cnt, w->gamma, w->gamma_prev, w->flag, w->nact, w->bar};
+                  w->conv, w->iters, w->cnt, w->gamma, w->gamma_prev, w->flag, w->nact, w->bar, w->gpart};
   for (void* p : ptrs) dfree(p, s);
   if (w->graph64) cudaGraphExecDestroy(w->graph64);
   if (w->graph32) cudaGraphExecDestroy(w->graph32);
@@ -1194,16 +1192,20 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
   SolverScratch* w = S->solver;
   const bool mixed = o->precision == ZI_MIXED;
   if (!w) {
+    int ld, c64, c32;
+    choose_layout(S->n_rhs, &ld, &c64, &c32);
+    int64_t nl = S->n * (int64_t)ld;
+    // vector offsets (row * ld / 2 for FP64 16-byte vectors) are 32-bit in the CG kernels
+    if (nl / 2 > (int64_t)INT32_MAX)
+      return set_error(ZI_ERR_ARG, "system too large: n * ld / 2 = %lld exceeds 32-bit vector offsets",
+                       (long long)(nl / 2));
     w = new SolverScratch();
     S->solver = w;
     ZI_CUDA(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
-    int ld, c64, c32;
-    choose_layout(S->n_rhs, &ld, &c64, &c32);
     w->ld = ld;
     w->ncol = S->n_rhs;
     w->n = S->n;
     w->nblk = (sm_count() * blocks_per_sm_for(0) + CLUSTER - 1) / CLUSTER * CLUSTER;
-    int64_t nl = S->n * (int64_t)ld;
     ZI_CHECK(dalloc_n(&w->s, S->n, s));
     ZI_CHECK(dalloc_n(&w->dtrue, S->n, s));
     ZI_CHECK(dalloc_n(&w->v64, S->nnz, s));
@@ -1636,9 +1638,18 @@ struct BatchHead {
   const double* dtrue;
   double *rho, *alpha, *beta, *stop2;
   int *conv, *iters, *cnt;
-  double *part0, *part1, *part2;
-  unsigned* bar;  // [0] arrivals, [1] generation
+  double *part0, *part1, *part2;     // per-block column partials
+  double *gpart0, *gpart1, *gpart2;  // per-group column sums
+  unsigned* bar;  // [0] arrivals, [1] generation, [2 + q] arrivals of group q
 };
+
+// Column reductions run as a two-level tree in a fixed order: the block that
+// arrives last in its group of BGROUP consecutive blocks sums the group's
+// partials in block order, and the block that arrives last at the head
+// barrier sums the group sums in group order.  The result does not depend on
+// which blocks happen to arrive last.
+constexpr int BGROUP = 16;
+__host__ __device__ inline int batch_groups(int nblk) { return (nblk + BGROUP - 1) / BGROUP; }
 
 constexpr long long BAR_SPIN_LIMIT = 2000000;  // a few seconds with the back-off below
 
@@ -1688,6 +1699,42 @@ __device__ __forceinline__ bool bar_wait(unsigned* bar, unsigned gen, int* err) 
   return s_ok != 0;
 }
 
+// Arrival in group q of gs blocks; true in the block that arrives last, which
+// re-arms the counter (every member has arrived, none arrives again before
+// the head barrier releases them).
+__device__ __forceinline__ bool group_last(unsigned* gcnt, int q, int gs) {
+  __shared__ int s_lead;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned a = atomicAdd(&gcnt[q], 1u);
+    const int lead = a == (unsigned)gs - 1u;
+    if (lead) {
+      atomicExch(&gcnt[q], 0u);
+      __threadfence();
+    }
+    s_lead = lead;
+  }
+  __syncthreads();
+  return s_lead != 0;
+}
+
+// Sum over rows [b0, b1) of part (row stride ld) at column col, in row order.
+// Other blocks wrote these rows in this launch: loads go through L2.
+__device__ __forceinline__ double rows_sum(const double* part, int b0, int b1, int ld, int col) {
+  double s = 0.0;
+  int b = b0;
+  for (; b + 8 <= b1; b += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(part + (int64_t)(b + u) * ld + col);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  for (; b < b1; ++b) s += __ldcg(part + (int64_t)b * ld + col);
+  return s;
+}
+
 // Column totals of this block into part[lb][0..ld) (runtime cptv <= CPTVMAX).
 template <int CPTVMAX, int W, typename AccT>
 __device__ __forceinline__ void batch_block_totals(AccT (&acc)[CPTVMAX][W], int g, int c, int rpb, int tpr, int cptv,
@@ -1707,25 +1754,35 @@ __device__ __forceinline__ void batch_block_totals(AccT (&acc)[CPTVMAX][W], int 
   }
 }
 
-__device__ __forceinline__ double batch_column_sum(const double* __restrict__ part, int nblk, int ld, int col) {
-  double s = 0.0;
-  int b = 0;
-  for (; b + 8 <= nblk; b += 8) {
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = part[(int64_t)(b + u) * ld + col];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) s += v[u];
+// Rows of one block of a head: chunks of 4 * rpb consecutive rows are dealt
+// to the head's blocks in turn, and row group g of a block takes rows g,
+// g + rpb, g + 2 rpb, g + 3 rpb of each of its chunks.  The walk is kept in
+// 32-bit registers: the row i and its slot k in the current chunk.
+struct BatchRows {
+  int n, rpb, jump;  // jump: from the last row of a chunk to the block's next chunk
+};
+__device__ __forceinline__ int brow_first(const BatchRows& w, int g, int lb) {
+  const int i = lb * 4 * w.rpb + g;
+  return (g < w.rpb && i < w.n) ? i : -1;
+}
+__device__ __forceinline__ int brow_next(const BatchRows& w, int i, int& k) {
+  if (++k < 4) {
+    i += w.rpb;
+  } else {
+    k = 0;
+    i += w.jump;
   }
-  for (; b < nblk; ++b) s += part[(int64_t)b * ld + col];
-  return s;
+  return i < w.n ? i : -1;
 }
 
+// One block of the batched solve runs `chunk` CG iterations on its head's
+// rows.  Every row of a head is split over ld / W threads, one 16-byte vector
+// (W columns) each, so the register budget allows four resident blocks per SM.
 // skip_block >= 0 (fault-injection test only): that block leaves before its
 // first barrier, as a failed block would; the other blocks of its head wait
 // out their bound, set DEV_ERR_TIMEOUT and return.
-template <typename T, int CPTVMAX>
-__global__ void __launch_bounds__(256, 2) k_cg_batched(const BatchHead<T>* __restrict__ heads,
+template <typename T>
+__global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __restrict__ heads,
                                                        const int* __restrict__ block_head, int chunk,
                                                        int* __restrict__ err, int skip_block) {
   using V = typename Vec<T>::type;
@@ -1740,15 +1797,11 @@ __global__ void __launch_bounds__(256, 2) k_cg_batched(const BatchHead<T>* __res
   __syncthreads();
   const BatchHead<T>& H = sH;
   const int lb = blockIdx.x - H.blk0;
-  const int tpr = H.tpr, cptv = H.cptv, nv = H.nv, ld = H.ld;
+  const int tpr = H.tpr, nv = H.nv, ld = H.ld;
   const int rpb = blockDim.x / tpr;
   const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
-  const RowWalk rw = row_walk_sub(H.n, rpb, g, lb, H.nblk);
-  const V* Pv = reinterpret_cast<const V*>(H.P);
-  V* Qv = reinterpret_cast<V*>(H.Q);
-  V* Rv = reinterpret_cast<V*>(H.R);
-  V* Xv = reinterpret_cast<V*>(H.X);
-  V* Pw = reinterpret_cast<V*>(H.P);
+  const BatchRows rw{(int)H.n, rpb, (H.nblk * 4 - 3) * rpb};
+  const int gq = lb / BGROUP, gb0 = gq * BGROUP, gb1 = min(gb0 + BGROUP, H.nblk);
   for (int it = 0; it < chunk; ++it) {
     if (threadIdx.x == 0) {
       const int active = atomicAdd(&H.cnt[0], 0);
@@ -1759,145 +1812,146 @@ __global__ void __launch_bounds__(256, 2) k_cg_batched(const BatchHead<T>* __res
     __syncthreads();
     if (s_stop) break;
     // ---- phase A: Q = A P, p.q partials
-    T acc_pq[CPTVMAX][W];
+    T acc_pq[1][W];
 #pragma unroll
-    for (int v = 0; v < CPTVMAX; ++v)
+    for (int k = 0; k < W; ++k) acc_pq[0][k] = T(0);
+    {
+      const V* Pc = reinterpret_cast<const V*>(H.P) + c;  // n * ld / 2 < 2^31 (host-checked)
+      V* Qc = reinterpret_cast<V*>(H.Q) + c;
+      bool ell = false;
+      if constexpr (sizeof(T) == 4) {
+        const int4* eci = H.ell_ci;
+        ell = eci != nullptr;
+        if (ell) {
+          // ELL rows: the next row's column indices are fetched behind the gathers
+          const float4* eva = H.ell_va;
+          int k = 0;
+          int i = brow_first(rw, g, lb);
+          int jn[ELL_K];
+          if (i >= 0) ell_cols(eci, i, jn);
+          while (i >= 0) {
+            int j[ELL_K];
 #pragma unroll
-      for (int k = 0; k < W; ++k) acc_pq[v][k] = T(0);
-    if constexpr (sizeof(T) == 4) {
-      if (H.ell_ci) {
-        // ELL rows: next row's column indices prefetched behind the gathers
-        int64_t i = rw_first(rw);
-        int jn[ELL_K];
-        if (i >= 0) ell_cols(H.ell_ci, i, jn);
-        while (i >= 0) {
-          int j[ELL_K];
+            for (int u = 0; u < ELL_K; ++u) j[u] = jn[u];
+            const bool tail = j[0] < 0;
+            j[0] = tail ? ~j[0] : j[0];
+            V x[ELL_K];
 #pragma unroll
-          for (int u = 0; u < ELL_K; ++u) j[u] = jn[u];
-          const bool tail = j[0] < 0;
-          j[0] = tail ? ~j[0] : j[0];
-          V x[ELL_K][CPTVMAX];
-#pragma unroll
-          for (int u = 0; u < ELL_K; ++u)
-#pragma unroll
-            for (int v = 0; v < CPTVMAX; ++v)
-              x[u][v] = (j[u] >= 0 && v < cptv) ? ldg_v(Pv + (j[u] * nv + c + v * tpr)) : vzero<V>();
-          const float4 a0 = __ldg(H.ell_va + i * (ELL_K / 4)), a1 = __ldg(H.ell_va + i * (ELL_K / 4) + 1);
-          const int64_t inext = rw_next(rw, i);
-          if (inext >= 0) ell_cols(H.ell_ci, inext, jn);
-          const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-#pragma unroll
-          for (int v = 0; v < CPTVMAX; ++v) {
-            if (v >= cptv) continue;
+            for (int u = 0; u < ELL_K; ++u) x[u] = j[u] >= 0 ? ldg_v(Pc + j[u] * nv) : vzero<V>();
+            const float4 a0 = __ldg(eva + i * (ELL_K / 4)), a1 = __ldg(eva + i * (ELL_K / 4) + 1);
+            const int inext = brow_next(rw, i, k);
+            if (inext >= 0) ell_cols(eci, inext, jn);
+            const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             V acc = vzero<V>();
 #pragma unroll
-            for (int u = 0; u < ELL_K; ++u) vfma(acc, a[u], x[u][v]);
+            for (int u = 0; u < ELL_K; ++u) vfma(acc, a[u], x[u]);
             if (tail) {
               const int t0 = __ldg(H.tail_ptr + i), t1 = __ldg(H.tail_ptr + i + 1);
-              for (int t = t0; t < t1; ++t)
-                vfma(acc, __ldg(H.tail_va + t), ldg_v(Pv + (__ldg(H.tail_ci + t) * nv + c + v * tpr)));
+              for (int t = t0; t < t1; ++t) vfma(acc, __ldg(H.tail_va + t), ldg_v(Pc + __ldg(H.tail_ci + t) * nv));
             }
-            Qv[i * nv + c + v * tpr] = acc;
+            Qc[i * nv] = acc;
 #pragma unroll
-            for (int kk = 0; kk < W; ++kk) acc_pq[v][kk] += vget(x[0][v], kk) * vget(acc, kk);
+            for (int kk = 0; kk < W; ++kk) acc_pq[0][kk] += vget(x[0], kk) * vget(acc, kk);
+            i = inext;
           }
-          i = inext;
+        }
+      }
+      if (!ell) {
+        const int32_t* rowptr = H.rowptr;
+        const int32_t* colind = H.colind;
+        const T* vals = H.vals;
+        int k = 0;
+        for (int i = brow_first(rw, g, lb); i >= 0; i = brow_next(rw, i, k)) {
+          V acc = vzero<V>();
+          const int r0 = __ldg(rowptr + i), r1 = __ldg(rowptr + i + 1);
+          for (int e = r0; e < r1; e += G) {
+            int j[G];
+            T a[G];
+            load_batch<T, G>(e, r1, colind, vals, j, a);
+            V x[G];
+#pragma unroll
+            for (int u = 0; u < G; ++u) x[u] = j[u] >= 0 ? ldg_v(Pc + j[u] * nv) : vzero<V>();
+#pragma unroll
+            for (int u = 0; u < G; ++u) vfma(acc, a[u], x[u]);
+          }
+          Qc[i * nv] = acc;
+          const V pv = ldg_v(Pc + i * nv);
+#pragma unroll
+          for (int kk = 0; kk < W; ++kk) acc_pq[0][kk] += vget(pv, kk) * vget(acc, kk);
         }
       }
     }
-    if (sizeof(T) == 8 || !H.ell_ci) {
-      for (int64_t i = rw_first(rw); i >= 0; i = rw_next(rw, i)) {
-        V acc[CPTVMAX];
-#pragma unroll
-        for (int v = 0; v < CPTVMAX; ++v) acc[v] = vzero<V>();
-        const int r0 = __ldg(H.rowptr + i), r1 = __ldg(H.rowptr + i + 1);
-        for (int k = r0; k < r1; k += G) {
-          int j[G];
-          T a[G];
-          load_batch<T, G>(k, r1, H.colind, H.vals, j, a);
-          V x[G][CPTVMAX];
-#pragma unroll
-          for (int u = 0; u < G; ++u)
-#pragma unroll
-            for (int v = 0; v < CPTVMAX; ++v)
-              x[u][v] = (j[u] >= 0 && v < cptv) ? ldg_v(Pv + (int64_t)j[u] * nv + c + v * tpr) : vzero<V>();
-#pragma unroll
-          for (int v = 0; v < CPTVMAX; ++v) {
-            if (v >= cptv) continue;
-#pragma unroll
-            for (int u = 0; u < G; ++u) vfma(acc[v], a[u], x[u][v]);
-          }
-        }
-#pragma unroll
-        for (int v = 0; v < CPTVMAX; ++v) {
-          if (v >= cptv) continue;
-          const int64_t o = i * nv + c + v * tpr;
-          Qv[o] = acc[v];
-          V p = ldg_v(Pv + o);
-#pragma unroll
-          for (int kk = 0; kk < W; ++kk) acc_pq[v][kk] += vget(p, kk) * vget(acc[v], kk);
-        }
-      }
-    }
-    batch_block_totals<CPTVMAX, W, T>(acc_pq, g, c, rpb, tpr, cptv, ld, sred, H.part0 + (int64_t)lb * ld);
+    batch_block_totals<1, W, T>(acc_pq, g, c, rpb, tpr, 1, ld, sred, H.part0 + (int64_t)lb * ld);
     bool last;
     if (it == 0 && (int)blockIdx.x == skip_block) return;  // injected fault: this block leaves
+    if (group_last(H.bar + 2, gq, gb1 - gb0))
+      for (int col = threadIdx.x; col < ld; col += blockDim.x)
+        H.gpart0[(int64_t)gq * ld + col] = rows_sum(H.part0, gb0, gb1, ld, col);
     unsigned gen = bar_arrive(H.bar, H.nblk, &last);
     if (last) {
+      const int ngr = batch_groups(H.nblk);
       for (int col = threadIdx.x; col < ld; col += blockDim.x) {
-        double sum = batch_column_sum(H.part0, H.nblk, ld, col);
+        double sum = rows_sum(H.gpart0, 0, ngr, ld, col);
         double a = 0.0;
-        if (col < H.ncol && !H.conv[col] && sum > 0.0 && isfinite(sum)) a = H.rho[col] / sum;
+        if (col < H.ncol && !__ldcg(H.conv + col) && sum > 0.0 && isfinite(sum)) a = __ldcg(H.rho + col) / sum;
         H.alpha[col] = a;
       }
       bar_release(H.bar);
     } else if (!bar_wait(H.bar, gen, err)) {
       return;
     }
-    for (int col = threadIdx.x; col < ld; col += blockDim.x) s_alpha[col] = H.alpha[col];
+    for (int col = threadIdx.x; col < ld; col += blockDim.x) s_alpha[col] = __ldcg(H.alpha + col);
     __syncthreads();
     // ---- phase B: r -= alpha q, r.r and D-weighted r.r partials
-    T rr[CPTVMAX][W], rd[CPTVMAX][W];
+    T rr[1][W], rd[1][W];
 #pragma unroll
-    for (int v = 0; v < CPTVMAX; ++v)
+    for (int k = 0; k < W; ++k) rr[0][k] = rd[0][k] = T(0);
+    {
+      const V* Qc = reinterpret_cast<const V*>(H.Q) + c;
+      V* Rc = reinterpret_cast<V*>(H.R) + c;
+      T al[W];
 #pragma unroll
-      for (int k = 0; k < W; ++k) rr[v][k] = rd[v][k] = T(0);
-    for (int64_t i = rw_first(rw); i >= 0; i = rw_next(rw, i)) {
-      const T di = (T)__ldg(H.dtrue + i);
+      for (int k = 0; k < W; ++k) al[k] = (T)s_alpha[c * W + k];
+      int k = 0;
+      for (int i = brow_first(rw, g, lb); i >= 0; i = brow_next(rw, i, k)) {
+        const T di = (T)__ldg(H.dtrue + i);
+        const V q = Qc[i * nv];
+        V r = Rc[i * nv];
 #pragma unroll
-      for (int v = 0; v < CPTVMAX; ++v) {
-        if (v >= cptv) continue;
-        const int64_t o = i * nv + c + v * tpr;
-        V q = Qv[o], r = Rv[o];
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-          T rv = vget(r, k) - (T)s_alpha[(c + v * tpr) * W + k] * vget(q, k);
-          vset(r, k, rv);
-          rr[v][k] += rv * rv;
-          rd[v][k] += di * rv * rv;
+        for (int u = 0; u < W; ++u) {
+          const T rv = vget(r, u) - al[u] * vget(q, u);
+          vset(r, u, rv);
+          rr[0][u] += rv * rv;
+          rd[0][u] += di * rv * rv;
         }
-        Rv[o] = r;
+        Rc[i * nv] = r;
       }
     }
-    batch_block_totals<CPTVMAX, W, T>(rr, g, c, rpb, tpr, cptv, ld, sred, H.part1 + (int64_t)lb * ld);
+    batch_block_totals<1, W, T>(rr, g, c, rpb, tpr, 1, ld, sred, H.part1 + (int64_t)lb * ld);
     __syncthreads();
-    batch_block_totals<CPTVMAX, W, T>(rd, g, c, rpb, tpr, cptv, ld, sred, H.part2 + (int64_t)lb * ld);
+    batch_block_totals<1, W, T>(rd, g, c, rpb, tpr, 1, ld, sred, H.part2 + (int64_t)lb * ld);
+    if (group_last(H.bar + 2, gq, gb1 - gb0))
+      for (int col = threadIdx.x; col < ld; col += blockDim.x) {
+        H.gpart1[(int64_t)gq * ld + col] = rows_sum(H.part1, gb0, gb1, ld, col);
+        H.gpart2[(int64_t)gq * ld + col] = rows_sum(H.part2, gb0, gb1, ld, col);
+      }
     gen = bar_arrive(H.bar, H.nblk, &last);
     if (last) {
       if (threadIdx.x == 0) s_nact = s_nreach = 0;
       __syncthreads();
-      const int itn = H.cnt[1] + 1;
+      const int ngr = batch_groups(H.nblk);
+      const int itn = __ldcg(H.cnt + 1) + 1;
       for (int col = threadIdx.x; col < ld; col += blockDim.x) {
-        double r2 = batch_column_sum(H.part1, H.nblk, ld, col);
-        double d2 = batch_column_sum(H.part2, H.nblk, ld, col);
+        double r2 = rows_sum(H.gpart1, 0, ngr, ld, col);
+        double d2 = rows_sum(H.gpart2, 0, ngr, ld, col);
         double be = 0.0;
-        if (col < H.ncol && !H.conv[col]) {
+        if (col < H.ncol && !__ldcg(H.conv + col)) {
           const bool hit = d2 <= H.stop2[col];
           if (!(r2 > 0.0) || (hit && H.freeze)) {
             H.conv[col] = 1;
             H.iters[col] = itn;
           } else {
-            be = r2 / H.rho[col];
+            be = r2 / __ldcg(H.rho + col);
             H.rho[col] = r2;
             H.iters[col] = itn;
             atomicAdd(&s_nact, 1);
@@ -1916,23 +1970,30 @@ __global__ void __launch_bounds__(256, 2) k_cg_batched(const BatchHead<T>* __res
     } else if (!bar_wait(H.bar, gen, err)) {
       return;
     }
-    for (int col = threadIdx.x; col < ld; col += blockDim.x) s_beta[col] = H.beta[col];
+    for (int col = threadIdx.x; col < ld; col += blockDim.x) s_beta[col] = __ldcg(H.beta + col);
     __syncthreads();
     // ---- phase C: x += alpha p, p = r + beta p
-    for (int64_t i = rw_first(rw); i >= 0; i = rw_next(rw, i)) {
+    {
+      const V* Rc = reinterpret_cast<const V*>(H.R) + c;
+      V* Pc = reinterpret_cast<V*>(H.P) + c;
+      V* Xc = reinterpret_cast<V*>(H.X) + c;
+      T al[W], be[W];
 #pragma unroll
-      for (int v = 0; v < CPTVMAX; ++v) {
-        if (v >= cptv) continue;
-        const int64_t o = i * nv + c + v * tpr;
-        V r = Rv[o], p = Pw[o], x = Xv[o];
+      for (int k = 0; k < W; ++k) {
+        al[k] = (T)s_alpha[c * W + k];
+        be[k] = (T)s_beta[c * W + k];
+      }
+      int k = 0;
+      for (int i = brow_first(rw, g, lb); i >= 0; i = brow_next(rw, i, k)) {
+        const V r = Rc[i * nv];
+        V p = Pc[i * nv], x = Xc[i * nv];
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-          const int col = (c + v * tpr) * W + k;
-          vset(x, k, vget(x, k) + (T)s_alpha[col] * vget(p, k));
-          vset(p, k, vget(r, k) + (T)s_beta[col] * vget(p, k));
+        for (int u = 0; u < W; ++u) {
+          vset(x, u, vget(x, u) + al[u] * vget(p, u));
+          vset(p, u, vget(r, u) + be[u] * vget(p, u));
         }
-        Xv[o] = x;
-        Pw[o] = p;
+        Xc[i * nv] = x;
+        Pc[i * nv] = p;
       }
     }
     gen = bar_arrive(H.bar, H.nblk, &last);
@@ -1944,17 +2005,38 @@ __global__ void __launch_bounds__(256, 2) k_cg_batched(const BatchHead<T>* __res
   }
 }
 
-// widest row split of a head (ld <= 256): FP32 2 vectors per thread, FP64 4
-template <typename T> struct BatchCptv { static constexpr int v = sizeof(T) == 4 ? 2 : 4; };
+static inline int nb_max_heads(int nh) { return nh < 64 ? 64 : nh; }
+
+
+// State kept across the chunks of one batched solve: the device copies of
+// the head descriptors and the block-to-head map, and the CUDA graph of one
+// chunk (barrier resets + the cooperative launch), re-captured only when the
+// set of active heads -- hence the block partition -- changes.  Descriptor
+// updates between chunks go to device memory the graph reads.
+struct BatchCtx {
+  std::vector<HeadRun*> act;  // active set of the captured graph
+  cudaGraphExec_t exec = nullptr;
+  void* d_heads = nullptr;
+  int* d_bh = nullptr;
+  int cap_heads = 0, cap_blocks = 0;
+  bool graphs = true;  // false once capture is refused: launch directly
+  cudaStream_t st = nullptr;
+  explicit BatchCtx(cudaStream_t s) : st(s) {}
+  ~BatchCtx() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (d_heads) dfree(d_heads, st);
+    if (d_bh) dfree(d_bh, st);
+  }
+};
 
 template <typename T>
-static int run_batched_chunk(std::vector<HeadRun*>& act, int chunk, cudaStream_t st, int* d_err) {
-  const void* fn = (const void*)k_cg_batched<T, BatchCptv<T>::v>;
+static int run_batched_chunk(std::vector<HeadRun*>& act, int chunk, cudaStream_t st, int* d_err, BatchCtx& ctx) {
+  const void* fn = (const void*)k_cg_batched<T>;
   // dynamic shared memory: the largest rpb * ld over the heads
   size_t smem = 0;
   for (HeadRun* h : act) {
-    const CgPlan& p = sizeof(T) == 4 ? h->p32 : h->p64;
-    smem = std::max(smem, sizeof(double) * (size_t)(BLOCK / p.tpr) * p.ld);
+    const int ld = h->S->solver->ld, tpr = ld / Vec<T>::W;
+    smem = std::max(smem, sizeof(double) * (size_t)(BLOCK / tpr) * ld);
   }
   ZI_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
@@ -1985,13 +2067,12 @@ static int run_batched_chunk(std::vector<HeadRun*>& act, int chunk, cudaStream_t
   for (int k = 0; k < nh; ++k) {
     HeadRun* h = act[k];
     SolverScratch* w = h->S->solver;
-    const CgPlan& p = sizeof(T) == 4 ? h->p32 : h->p64;
     BatchHead<T>& b = hh[k];
     b.n = h->S->n;
     b.ld = w->ld;
     b.nv = w->ld / Vec<T>::W;
-    b.tpr = p.tpr;
-    b.cptv = p.cptv;
+    b.tpr = w->ld / Vec<T>::W;
+    b.cptv = 1;
     b.ncol = h->S->n_rhs;
     b.blk0 = blk;
     b.nblk = nb[k];
@@ -2023,28 +2104,80 @@ static int run_batched_chunk(std::vector<HeadRun*>& act, int chunk, cudaStream_t
     b.rho = w->rho; b.alpha = w->alpha; b.beta = w->beta; b.stop2 = w->stop2;
     b.conv = w->conv; b.iters = w->iters; b.cnt = w->cnt;
     b.part0 = w->part0; b.part1 = w->part1; b.part2 = w->part2;
+    b.gpart0 = w->gpart;
+    b.gpart1 = w->gpart + (int64_t)batch_groups(w->nblk) * w->ld;
+    b.gpart2 = w->gpart + 2 * (int64_t)batch_groups(w->nblk) * w->ld;
     b.bar = w->bar;
     for (int q = 0; q < nb[k]; ++q) bh.push_back(k);
     blk += nb[k];
-    ZI_CUDA(cudaMemsetAsync(w->bar, 0, 2 * sizeof(unsigned), st));
   }
-  DevTmp<BatchHead<T>> d_heads;
-  DevTmp<int> d_bh;
-  ZI_CHECK(d_heads.alloc(nh, st));
-  ZI_CHECK(d_bh.alloc(bh.size(), st));
-  ZI_CUDA(cudaMemcpyAsync(d_heads.p, hh.data(), sizeof(BatchHead<T>) * nh, cudaMemcpyHostToDevice, st));
-  ZI_CUDA(cudaMemcpyAsync(d_bh.p, bh.data(), sizeof(int) * bh.size(), cudaMemcpyHostToDevice, st));
-  const BatchHead<T>* a0 = d_heads.p;
-  const int* a1 = d_bh.p;
+  // device copies of the descriptors (grown as needed)
+  if (ctx.cap_heads < nh) {
+    if (ctx.d_heads) dfree(ctx.d_heads, st);
+    ctx.d_heads = nullptr;
+    ZI_CHECK(dalloc(&ctx.d_heads, sizeof(BatchHead<double>) * nb_max_heads(nh), st));
+    ctx.cap_heads = nb_max_heads(nh);
+  }
+  if (ctx.cap_blocks < (int)bh.size()) {
+    if (ctx.d_bh) dfree(ctx.d_bh, st);
+    ctx.d_bh = nullptr;
+    ZI_CHECK(dalloc_n(&ctx.d_bh, bh.size(), st));
+    ctx.cap_blocks = (int)bh.size();
+  }
+  ZI_CUDA(cudaMemcpyAsync(ctx.d_heads, hh.data(), sizeof(BatchHead<T>) * nh, cudaMemcpyHostToDevice, st));
+  const BatchHead<T>* a0 = static_cast<const BatchHead<T>*>(ctx.d_heads);
+  const int* a1 = ctx.d_bh;
   int a2 = chunk;
   int* a3 = d_err;
   // test-only fault injection (ZI_TEST_BARRIER_SKIP=1): block 0 leaves before its first barrier
   const char* fe = getenv("ZI_TEST_BARRIER_SKIP");
   int a4 = (fe && fe[0] == '1') ? 0 : -1;
   void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3, (void*)&a4};
-  ZI_CUDA(cudaLaunchCooperativeKernel(fn, dim3(blk), dim3(BLOCK), args, smem, st));
+  auto record = [&](cudaStream_t cs) -> int {
+    for (HeadRun* h : act)
+      ZI_CUDA(cudaMemsetAsync(h->S->solver->bar, 0, (2 + batch_groups(h->S->solver->nblk)) * sizeof(unsigned), cs));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blk);
+    cfg.blockDim = dim3(BLOCK);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = cs;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeCooperative;
+    attr.val.cooperative = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    ZI_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+    return ZI_OK;
+  };
+  const bool same = ctx.exec && ctx.act == act && a4 < 0;
+  if (!same) {
+    if (ctx.exec) {
+      cudaGraphExecDestroy(ctx.exec);
+      ctx.exec = nullptr;
+    }
+    ZI_CUDA(cudaMemcpyAsync(ctx.d_bh, bh.data(), sizeof(int) * bh.size(), cudaMemcpyHostToDevice, st));
+    if (ctx.graphs && a4 < 0) {
+      cudaGraph_t g = nullptr;
+      ZI_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      int rs = record(st);
+      cudaError_t e = cudaStreamEndCapture(st, &g);
+      if (rs == ZI_OK && e == cudaSuccess && cudaGraphInstantiate(&ctx.exec, g, 0) == cudaSuccess) {
+        ctx.act = act;
+      } else {
+        ctx.exec = nullptr;
+        ctx.graphs = false;  // capture refused: launch directly from now on
+      }
+      if (g) cudaGraphDestroy(g);
+      (void)cudaGetLastError();
+    }
+  }
+  if (ctx.exec) {
+    ZI_CUDA(cudaGraphLaunch(ctx.exec, st));
+  } else {
+    ZI_CHECK(record(st));
+  }
   count_launches(1);
-  ZI_CUDA(cudaStreamSynchronize(st));  // host arrays above die with this frame
+  ZI_CUDA(cudaStreamSynchronize(st));  // the host descriptor arrays die with this frame
   return ZI_OK;
 }
 
@@ -2060,6 +2193,7 @@ int transfer_batched_impl(zi_system* const* sys, int nb, const zi_solver_opts* o
   int status = ZI_OK;
   auto run = [&]() -> int {
     DevTmp<int> d_err;
+    BatchCtx ctx(st);
     ZI_CHECK(d_err.alloc(1, st));
     ZI_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int), st));
     for (int b = 0; b < nb; ++b) {
@@ -2067,7 +2201,9 @@ int transfer_batched_impl(zi_system* const* sys, int nb, const zi_solver_opts* o
       heads[b].o = o;
       heads[b].st = st;
       ZI_CHECK(ensure_scratch(sys[b], o, st));
-      if (!sys[b]->solver->bar) ZI_CHECK(dalloc_n(&sys[b]->solver->bar, 2, st));
+      SolverScratch* w = sys[b]->solver;
+      if (!w->bar) ZI_CHECK(dalloc_n(&w->bar, 2 + batch_groups(w->nblk), st));
+      if (!w->gpart) ZI_CHECK(dalloc_n(&w->gpart, 3 * (size_t)batch_groups(w->nblk) * w->ld, st));
       ZI_CHECK(head_begin(heads[b]));
     }
     const int chunk = o->check_every > 0 ? o->check_every : 25;
@@ -2078,9 +2214,9 @@ int transfer_batched_impl(zi_system* const* sys, int nb, const zi_solver_opts* o
         if (!h.done) act.push_back(&h);
       if (act.empty()) break;
       if (mixed)
-        ZI_CHECK(run_batched_chunk<float>(act, chunk, st, d_err.p));
+        ZI_CHECK(run_batched_chunk<float>(act, chunk, st, d_err.p, ctx));
       else
-        ZI_CHECK(run_batched_chunk<double>(act, chunk, st, d_err.p));
+        ZI_CHECK(run_batched_chunk<double>(act, chunk, st, d_err.p, ctx));
       int herr = 0;
       ZI_CUDA(cudaMemcpyAsync(&herr, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
       ZI_CUDA(cudaStreamSynchronize(st));
