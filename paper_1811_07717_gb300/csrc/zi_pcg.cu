@@ -111,30 +111,32 @@ __device__ __forceinline__ void cluster_column_store(double* stot, int ld, doubl
   cl.sync();
 }
 
-// Rows are dealt to blocks in chunks of C = 4*rpb consecutive rows, round
-// robin: block b takes chunks b, b + G, b + 2G, ... (G blocks), and inside a
-// chunk row group g takes rows g, g + rpb, ...  The whole grid sweeps the
-// matrix together, so the P rows that neighbouring rows gather stay in L2,
-// while the consecutive rows of a chunk share them through L1.  The mapping
-// is fixed, so every reduction has a fixed order.
+// Rows are dealt to blocks in chunks of 4*rpb consecutive rows, round robin:
+// block b takes chunks b, b + G, b + 2G, ... (G blocks), and inside a chunk
+// row group g takes rows g, g + rpb, g + 2 rpb, g + 3 rpb.  The whole grid
+// sweeps the matrix together, so the P rows that neighbouring rows gather
+// stay in L2, while the consecutive rows of a chunk share them through L1.
+// The mapping is fixed, so every reduction has a fixed order.  The walk is
+// kept in 32-bit registers (rows < 2^31): the row i and its slot in the chunk.
 struct RowWalk {
-  int64_t n;
-  int C, rpb, g;
-  int blk, nblk;  // this block's index among the nblk blocks sharing the rows
+  int n, rpb, g, first;
+  int jump;  // from the last row of a chunk to the block's next chunk
 };
+__device__ __forceinline__ RowWalk row_walk_of(int64_t n, int rpb, int g, int blk, int nblk) {
+  return RowWalk{(int)n, rpb, g, blk * 4 * rpb + g, (nblk * 4 - 3) * rpb};
+}
 __device__ __forceinline__ RowWalk row_walk(int64_t n, int rpb, int g) {
-  return RowWalk{n, 4 * rpb, rpb, g, (int)blockIdx.x, (int)gridDim.x};
+  return row_walk_of(n, rpb, g, (int)blockIdx.x, (int)gridDim.x);
 }
-__device__ __forceinline__ int64_t rw_first(const RowWalk& w) {
-  int64_t i = (int64_t)w.blk * w.C + w.g;
-  return (w.g < w.rpb && i < w.n) ? i : -1;
-}
-__device__ __forceinline__ int64_t rw_next(const RowWalk& w, int64_t i) {
-  int64_t base = i - i % w.C;
-  int64_t nx = i + w.rpb;
-  if (nx < base + w.C) return nx < w.n ? nx : -1;
-  nx = base + (int64_t)w.nblk * w.C + w.g;
-  return nx < w.n ? nx : -1;
+__device__ __forceinline__ int rw_first(const RowWalk& w) { return (w.g < w.rpb && w.first < w.n) ? w.first : -1; }
+__device__ __forceinline__ int rw_next(const RowWalk& w, int i, int& slot) {
+  if (++slot < 4) {
+    i += w.rpb;
+  } else {
+    slot = 0;
+    i += w.jump;
+  }
+  return i < w.n ? i : -1;
 }
 
 // Early exit inside a replayed chunk of iterations: once no column is active
@@ -166,13 +168,13 @@ __device__ __forceinline__ void load_batch(int k0, int k1, const int32_t* __rest
 // acc += sum_u a[u] P[j[u]] over one batch; pown picks up P[i] (the diagonal
 // entry, present in every row) for the p.q dot.
 template <typename T, typename V, int G, int CPTV>
-__device__ __forceinline__ void gather_fma(const V* __restrict__ Pv, int nv, int tpr, int64_t i, const int (&j)[G],
+__device__ __forceinline__ void gather_fma(const V* __restrict__ Pv, int nv, int tpr, int i, const int (&j)[G],
                                            const T (&a)[G], V (&acc)[CPTV], V (&pown)[CPTV]) {
   V x[G][CPTV];
 #pragma unroll
   for (int u = 0; u < G; ++u)
 #pragma unroll
-    for (int v = 0; v < CPTV; ++v) x[u][v] = j[u] >= 0 ? ldg_v(Pv + (int64_t)j[u] * nv + v * tpr) : vzero<V>();
+    for (int v = 0; v < CPTV; ++v) x[u][v] = j[u] >= 0 ? ldg_v(Pv + (j[u] * nv + v * tpr)) : vzero<V>();
 #pragma unroll
   for (int u = 0; u < G; ++u) {
 #pragma unroll
@@ -212,7 +214,8 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
   const V* Pv = reinterpret_cast<const V*>(P) + c;
   V* Qv = reinterpret_cast<V*>(Q) + c;
   const RowWalk rw = row_walk(n, rpb, g);
-  int64_t i = rw_first(rw);
+  int slot = 0;
+  int i = rw_first(rw);
   bool active = i >= 0;
   int r0 = 0, r1 = 0;
   if (active) {
@@ -230,7 +233,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
       j[u] = jn[u];
       a[u] = an[u];
     }
-    const int64_t inext = rw_next(rw, i);
+    const int inext = rw_next(rw, i, slot);
     const bool more = inext >= 0;
     int n0 = 0, n1 = 0;
     if (more) {
@@ -269,7 +272,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
 // and P[i] for the p.q dot is the slot-0 gather.
 constexpr int ELL_K = 8;
 
-__device__ __forceinline__ void ell_cols(const int4* __restrict__ ci, int64_t i, int (&j)[ELL_K]) {
+__device__ __forceinline__ void ell_cols(const int4* __restrict__ ci, int i, int (&j)[ELL_K]) {
 #pragma unroll
   for (int q = 0; q < ELL_K / 4; ++q) {
     int4 c = __ldg(ci + i * (ELL_K / 4) + q);
@@ -307,7 +310,8 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
   const V* Pv = reinterpret_cast<const V*>(P) + c;
   V* Qv = reinterpret_cast<V*>(Q) + c;
   const RowWalk rw = row_walk(n, rpb, g);
-  int64_t i = rw_first(rw);
+  int slot = 0;
+  int i = rw_first(rw);
   bool active = i >= 0;
   int jn[ELL_K];
   if (active) ell_cols(ci, i, jn);
@@ -324,7 +328,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
       for (int v = 0; v < CPTV; ++v)
         x[u][v] = j[u] >= 0 ? ldg_v(Pv + (j[u] * nv + v * tpr)) : vzero<V>();  // n*ld/2 < 2^31 (host-checked)
     const float4 a0 = __ldg(va + i * (ELL_K / 4)), a1 = __ldg(va + i * (ELL_K / 4) + 1);
-    const int64_t inext = rw_next(rw, i);
+    const int inext = rw_next(rw, i, slot);
     const bool more = inext >= 0;
     if (more) ell_cols(ci, inext, jn);
     const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
@@ -385,11 +389,12 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
   V* Rv = reinterpret_cast<V*>(R);
   const RowWalk rw = row_walk(n, rpb, g);
   {
-    for (int64_t i = rw_first(rw); i >= 0; i = rw_next(rw, i)) {
+    int slot = 0;
+    for (int i = rw_first(rw); i >= 0; i = rw_next(rw, i, slot)) {
       const T di = (T)__ldg(dtrue + i);
 #pragma unroll
       for (int v = 0; v < CPTV; ++v) {
-        const int64_t o = i * nv + c + v * tpr;
+        const int o = i * nv + c + v * tpr;
         V q = ldg_v(Qv + o), r = Rv[o];
 #pragma unroll
         for (int k = 0; k < W; ++k) {
@@ -432,10 +437,11 @@ __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, int tpr, int ld, cons
   V* Pv = reinterpret_cast<V*>(P);
   V* Xv = reinterpret_cast<V*>(X);
   const RowWalk rw = row_walk(n, rpb, g);
-  for (int64_t i = rw_first(rw); i >= 0; i = rw_next(rw, i)) {
+  int slot = 0;
+  for (int i = rw_first(rw); i >= 0; i = rw_next(rw, i, slot)) {
 #pragma unroll
     for (int v = 0; v < CPTV; ++v) {
-      const int64_t o = i * nv + c + v * tpr;
+      const int o = i * nv + c + v * tpr;
       V r = ldg_v(Rv + o), p = Pv[o], x = Xv[o];
 #pragma unroll
       for (int k = 0; k < W; ++k) {
@@ -1754,27 +1760,6 @@ __device__ __forceinline__ void batch_block_totals(AccT (&acc)[CPTVMAX][W], int 
   }
 }
 
-// Rows of one block of a head: chunks of 4 * rpb consecutive rows are dealt
-// to the head's blocks in turn, and row group g of a block takes rows g,
-// g + rpb, g + 2 rpb, g + 3 rpb of each of its chunks.  The walk is kept in
-// 32-bit registers: the row i and its slot k in the current chunk.
-struct BatchRows {
-  int n, rpb, jump;  // jump: from the last row of a chunk to the block's next chunk
-};
-__device__ __forceinline__ int brow_first(const BatchRows& w, int g, int lb) {
-  const int i = lb * 4 * w.rpb + g;
-  return (g < w.rpb && i < w.n) ? i : -1;
-}
-__device__ __forceinline__ int brow_next(const BatchRows& w, int i, int& k) {
-  if (++k < 4) {
-    i += w.rpb;
-  } else {
-    k = 0;
-    i += w.jump;
-  }
-  return i < w.n ? i : -1;
-}
-
 // One block of the batched solve runs `chunk` CG iterations on its head's
 // rows.  Every row of a head is split over ld / W threads, one 16-byte vector
 // (W columns) each, so the register budget allows four resident blocks per SM.
@@ -1800,7 +1785,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
   const int tpr = H.tpr, nv = H.nv, ld = H.ld;
   const int rpb = blockDim.x / tpr;
   const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
-  const BatchRows rw{(int)H.n, rpb, (H.nblk * 4 - 3) * rpb};
+  const RowWalk rw = row_walk_of(H.n, rpb, g, lb, H.nblk);  // the walk of row_walk over the head's blocks
   const int gq = lb / BGROUP, gb0 = gq * BGROUP, gb1 = min(gb0 + BGROUP, H.nblk);
   for (int it = 0; it < chunk; ++it) {
     if (threadIdx.x == 0) {
@@ -1826,7 +1811,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
           // ELL rows: the next row's column indices are fetched behind the gathers
           const float4* eva = H.ell_va;
           int k = 0;
-          int i = brow_first(rw, g, lb);
+          int i = rw_first(rw);
           int jn[ELL_K];
           if (i >= 0) ell_cols(eci, i, jn);
           while (i >= 0) {
@@ -1839,7 +1824,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
 #pragma unroll
             for (int u = 0; u < ELL_K; ++u) x[u] = j[u] >= 0 ? ldg_v(Pc + j[u] * nv) : vzero<V>();
             const float4 a0 = __ldg(eva + i * (ELL_K / 4)), a1 = __ldg(eva + i * (ELL_K / 4) + 1);
-            const int inext = brow_next(rw, i, k);
+            const int inext = rw_next(rw, i, k);
             if (inext >= 0) ell_cols(eci, inext, jn);
             const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             V acc = vzero<V>();
@@ -1861,7 +1846,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
         const int32_t* colind = H.colind;
         const T* vals = H.vals;
         int k = 0;
-        for (int i = brow_first(rw, g, lb); i >= 0; i = brow_next(rw, i, k)) {
+        for (int i = rw_first(rw); i >= 0; i = rw_next(rw, i, k)) {
           V acc = vzero<V>();
           const int r0 = __ldg(rowptr + i), r1 = __ldg(rowptr + i + 1);
           for (int e = r0; e < r1; e += G) {
@@ -1913,7 +1898,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
 #pragma unroll
       for (int k = 0; k < W; ++k) al[k] = (T)s_alpha[c * W + k];
       int k = 0;
-      for (int i = brow_first(rw, g, lb); i >= 0; i = brow_next(rw, i, k)) {
+      for (int i = rw_first(rw); i >= 0; i = rw_next(rw, i, k)) {
         const T di = (T)__ldg(H.dtrue + i);
         const V q = Qc[i * nv];
         V r = Rc[i * nv];
@@ -1984,7 +1969,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
         be[k] = (T)s_beta[c * W + k];
       }
       int k = 0;
-      for (int i = brow_first(rw, g, lb); i >= 0; i = brow_next(rw, i, k)) {
+      for (int i = rw_first(rw); i >= 0; i = rw_next(rw, i, k)) {
         const V r = Rc[i * nv];
         V p = Pc[i * nv], x = Xc[i * nv];
 #pragma unroll
