@@ -97,6 +97,7 @@ __device__ __forceinline__ void block_column_totals(AccT (&acc)[CPTV][W], int g,
 // read gridDim/CLUSTER partials instead of one per block.
 constexpr int CLUSTER = 8;
 constexpr int MAX_LD = 256;
+constexpr int BLOCK_THREADS = 256;  // threads of every CG kernel block
 __device__ __forceinline__ void cluster_column_store(double* stot, int ld, double* out) {
   cg::cluster_group cl = cg::this_cluster();
   cl.sync();
@@ -280,28 +281,84 @@ __device__ __forceinline__ void ell_cols(const int4* __restrict__ ci, int i, int
   }
 }
 
+// The ELL slots of a block's rows are staged in shared memory by the TMA bulk
+// copy engine, a chunk of C = slots * rpb consecutive rows at a time, in a
+// ring of ELL_NBUF buffers: the copy of the block's next chunk is in flight
+// while the current one is processed, so the column indices a row's gathers
+// depend on are already on chip (loading them from HBM per row put one HBM
+// round trip in front of every row's gathers).
+constexpr int ELL_NBUF = 2;
+__host__ __device__ inline int ell_chunk_slots(int rpb) {
+  const int sl = 128 / rpb;
+  return sl < 1 ? 1 : (sl > 4 ? 4 : sl);
+}
+__host__ __device__ inline size_t ell_sred_bytes(int tpr, int ld) {
+  return ((size_t)(BLOCK_THREADS / tpr) * ld * sizeof(double) + 127) / 128 * 128;
+}
+__host__ __device__ inline size_t ell_smem_bytes(int tpr, int ld) {
+  const int rpb = BLOCK_THREADS / tpr;
+  const size_t C = (size_t)ell_chunk_slots(rpb) * rpb;
+  return ell_sred_bytes(tpr, ld) + (size_t)ELL_NBUF * 2 * C * 32;  // ci (int4 x 2) + va (float4 x 2) per row
+}
+
+constexpr long long MBAR_SPIN_LIMIT = 1 << 22;  // a few ms of polling before a copy is given up on
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for phase `parity` of bar; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (long long k = 0; k < MBAR_SPIN_LIMIT; ++k)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+
 // Slot 0 holds the diagonal's column i, stored as ~i (negative) when the row
-// continues in the tail.
+// continues in the tail.  Chunk t of block b covers rows (b + t G) C ...
+// + C - 1 (G blocks); row group g takes rows g, g + rpb, ... of a chunk.  On a
+// copy that never completes the kernel sets DEV_ERR_TIMEOUT in *err, waits
+// (bounded) for its other copies and still joins the cluster reduction.
 template <int CPTV>
-#ifndef ZI_ELL_MINB
-#define ZI_ELL_MINB 4
-#endif
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1 ? ZI_ELL_MINB : 2)
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1 ? 4 : 2)
     k_spmm_ell(int64_t n, int tpr, const int4* __restrict__ ci, const float4* __restrict__ va,
                const int32_t* __restrict__ tail_ptr, const int32_t* __restrict__ tail_ci,
                const float* __restrict__ tail_va, const float* __restrict__ P, float* __restrict__ Q, int ld,
-               double* __restrict__ partial, int* __restrict__ cnt, int freeze) {
+               double* __restrict__ partial, int* __restrict__ cnt, int freeze, int* __restrict__ err) {
   if (run_stopped(cnt, freeze)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) cnt[3] = 1;
     return;
   }
   using V = float4;
   constexpr int W = 4;
-  extern __shared__ double sred[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double* sred = reinterpret_cast<double*>(smem_raw);
   __shared__ double stot[MAX_LD];
+  __shared__ __align__(8) uint64_t bar[ELL_NBUF];
   const int nv = ld / W;
   const int rpb = blockDim.x / tpr;
   const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
+  const int slots = ell_chunk_slots(rpb), C = slots * rpb;
+  int4* sci = reinterpret_cast<int4*>(smem_raw + ell_sred_bytes(tpr, ld));  // [ELL_NBUF][2 C]
+  float4* sva = reinterpret_cast<float4*>(sci + ELL_NBUF * 2 * C);           // [ELL_NBUF][2 C]
   float acc_pq[CPTV][W];
 #pragma unroll
   for (int v = 0; v < CPTV; ++v)
@@ -309,53 +366,81 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
     for (int k = 0; k < W; ++k) acc_pq[v][k] = 0.f;
   const V* Pv = reinterpret_cast<const V*>(P) + c;
   V* Qv = reinterpret_cast<V*>(Q) + c;
-  const RowWalk rw = row_walk(n, rpb, g);
-  int slot = 0;
-  int i = rw_first(rw);
-  bool active = i >= 0;
-  int jn[ELL_K];
-  if (active) ell_cols(ci, i, jn);
-  while (active) {
-    int j[ELL_K];
+  const int64_t stride = (int64_t)gridDim.x * C, base0 = (int64_t)blockIdx.x * C;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < ELL_NBUF; ++b) mbar_init(&bar[b]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int b, int64_t cb) {  // one thread: copy chunk cb's slots into buffer b
+    const unsigned bytes = (unsigned)min((int64_t)C, n - cb) * 32u;
+    mbar_expect_tx(&bar[b], 2u * bytes);
+    bulk_g2s(sci + b * 2 * C, ci + 2 * cb, bytes, &bar[b]);
+    bulk_g2s(sva + b * 2 * C, va + 2 * cb, bytes, &bar[b]);
+  };
+  if (threadIdx.x == 0)
+    for (int b = 0; b < ELL_NBUF; ++b)
+      if (base0 + b * stride < n) issue(b, base0 + b * stride);
+  int use = 0;
+  bool ok = true;
+  for (int64_t base = base0; base < n; base += stride, ++use) {
+    const int b = use % ELL_NBUF;
+    ok = __syncthreads_and(mbar_wait(&bar[b], (unsigned)(use / ELL_NBUF) & 1u)) != 0;
+    if (!ok) break;
+    const int4* bc = sci + b * 2 * C;
+    const float4* bv = sva + b * 2 * C;
+    if (g < rpb) {
+      for (int k = 0; k < slots; ++k) {
+        const int lr = g + k * rpb;
+        const int i = (int)(base + lr);
+        if (base + lr >= n) break;
+        const int4 c0 = bc[2 * lr], c1 = bc[2 * lr + 1];
+        int j[ELL_K] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+        const bool tail = j[0] < 0;
+        j[0] = tail ? ~j[0] : j[0];
+        V x[ELL_K][CPTV];
 #pragma unroll
-    for (int u = 0; u < ELL_K; ++u) j[u] = jn[u];
-    const bool tail = j[0] < 0;
-    j[0] = tail ? ~j[0] : j[0];
-    V x[ELL_K][CPTV];
+        for (int u = 0; u < ELL_K; ++u)
 #pragma unroll
-    for (int u = 0; u < ELL_K; ++u)
+          for (int v = 0; v < CPTV; ++v)
+            x[u][v] = j[u] >= 0 ? ldg_v(Pv + (j[u] * nv + v * tpr)) : vzero<V>();  // n*ld/2 < 2^31 (host-checked)
+        const float4 a0 = bv[2 * lr], a1 = bv[2 * lr + 1];
+        const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        V acc[CPTV];
 #pragma unroll
-      for (int v = 0; v < CPTV; ++v)
-        x[u][v] = j[u] >= 0 ? ldg_v(Pv + (j[u] * nv + v * tpr)) : vzero<V>();  // n*ld/2 < 2^31 (host-checked)
-    const float4 a0 = __ldg(va + i * (ELL_K / 4)), a1 = __ldg(va + i * (ELL_K / 4) + 1);
-    const int inext = rw_next(rw, i, slot);
-    const bool more = inext >= 0;
-    if (more) ell_cols(ci, inext, jn);
-    const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    V acc[CPTV];
+        for (int v = 0; v < CPTV; ++v) {
+          acc[v] = vzero<V>();
 #pragma unroll
-    for (int v = 0; v < CPTV; ++v) {
-      acc[v] = vzero<V>();
+          for (int u = 0; u < ELL_K; ++u) vfma(acc[v], a[u], x[u][v]);
+        }
+        if (tail) {
+          const int t0 = __ldg(tail_ptr + i), t1 = __ldg(tail_ptr + i + 1);
+          for (int t = t0; t < t1; ++t) {
+            const int jj = __ldg(tail_ci + t);
+            const float aa = __ldg(tail_va + t);
 #pragma unroll
-      for (int u = 0; u < ELL_K; ++u) vfma(acc[v], a[u], x[u][v]);
-    }
-    if (tail) {
-      const int t0 = __ldg(tail_ptr + i), t1 = __ldg(tail_ptr + i + 1);
-      for (int t = t0; t < t1; ++t) {
-        const int jj = __ldg(tail_ci + t);
-        const float aa = __ldg(tail_va + t);
+            for (int v = 0; v < CPTV; ++v) vfma(acc[v], aa, ldg_v(Pv + (jj * nv + v * tpr)));
+          }
+        }
 #pragma unroll
-        for (int v = 0; v < CPTV; ++v) vfma(acc[v], aa, ldg_v(Pv + (int64_t)jj * nv + v * tpr));
+        for (int v = 0; v < CPTV; ++v) {
+          Qv[i * nv + v * tpr] = acc[v];
+#pragma unroll
+          for (int kk = 0; kk < W; ++kk) acc_pq[v][kk] += vget(x[0][v], kk) * vget(acc[v], kk);
+        }
       }
     }
-#pragma unroll
-    for (int v = 0; v < CPTV; ++v) {
-      Qv[i * nv + v * tpr] = acc[v];
-#pragma unroll
-      for (int kk = 0; kk < W; ++kk) acc_pq[v][kk] += vget(x[0][v], kk) * vget(acc[v], kk);
+    __syncthreads();  // buffer b consumed by every thread
+    if (threadIdx.x == 0 && base + ELL_NBUF * stride < n) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(b, base + ELL_NBUF * stride);
     }
-    i = inext;
-    active = more;
+  }
+  if (!ok && threadIdx.x == 0) {
+    atomicOr(err, DEV_ERR_TIMEOUT);
+    // copies still in flight: uses use .. use + ELL_NBUF - 1 that were issued
+    for (int u = use; u < use + ELL_NBUF; ++u)
+      if (base0 + u * stride < n) (void)mbar_wait(&bar[u % ELL_NBUF], (unsigned)(u / ELL_NBUF) & 1u);
   }
   block_column_totals<CPTV, W, float>(acc_pq, g, c, rpb, tpr, ld, sred, stot);
   cluster_column_store(stot, ld, partial);
@@ -904,12 +989,14 @@ void choose_layout(int ncol, int* ld, int* cptv64, int* cptv32) {
   else if (ncol <= 256) l = (ncol + 15) / 16 * 16;
   else l = (ncol + 31) / 32 * 32;
   *ld = l;
-  // vectors per row: l/2 (FP64), l/4 (FP32); at most 32 threads per row
+  // vectors per row: l/2 (FP64), l/4 (FP32); at most 32 threads per row for
+  // FP64 and 64 for FP32 (one vector per thread up to 256 columns keeps the
+  // FP32 SpMM at 4 resident blocks per SM)
   int nv64 = l / 2, nv32 = l / 4;
   int c64 = 1;
   while ((nv64 / c64 > 32 || nv64 % c64) && c64 < 64) c64 *= 2;
   int c32 = 1;
-  while ((nv32 / c32 > 32 || nv32 % c32) && c32 < 64) c32 *= 2;
+  while ((nv32 / c32 > 64 || nv32 % c32) && c32 < 64) c32 *= 2;
   *cptv64 = c64;
   *cptv32 = c32;
 }
@@ -940,13 +1027,13 @@ int launch_spmm(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int6
 
 int launch_spmm_ell(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, const int32_t* ci,
                     const float* va, const int32_t* tptr, const int32_t* tci, const float* tva, const float* P,
-                    float* Q, int ld, double* part, int* cnt = nullptr, int freeze = 1) {
+                    float* Q, int ld, double* part, int* err, int* cnt = nullptr, int freeze = 1) {
   const int4* c4 = reinterpret_cast<const int4*>(ci);
   const float4* v4 = reinterpret_cast<const float4*>(va);
   switch (cptv) {
-    case 1: k_spmm_ell<1><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part, cnt, freeze); break;
-    case 2: k_spmm_ell<2><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part, cnt, freeze); break;
-    case 4: k_spmm_ell<4><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part, cnt, freeze); break;
+    case 1: k_spmm_ell<1><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part, cnt, freeze, err); break;
+    case 2: k_spmm_ell<2><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part, cnt, freeze, err); break;
+    case 4: k_spmm_ell<4><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part, cnt, freeze, err); break;
     default: return set_error(ZI_ERR_ARG, "unsupported column layout");
   }
   ZI_LAUNCH_CHECK();
@@ -1004,6 +1091,8 @@ struct CgPlan {
   int ld, ncol, tpr, cptv, nblk;
   int g_spmm = 0, g_resid = 0, g_dir = 0;  // resident-grid sizes of the per-iteration kernels
   size_t smem;
+  size_t smem_ell = 0;   // dynamic shared memory of the ELL SpMM (reductions + staging ring)
+  int* err = nullptr;    // device error word of the solver (cnt[4])
   const int32_t* rowptr;
   const int32_t* colind;
   const int32_t* ell_ci = nullptr;  // FP32 ELL copy (null: CSR)
@@ -1086,7 +1175,12 @@ static const void* dir_fn(int cptv) {
 template <typename T>
 static void size_grids(CgPlan& p) {
   const bool ell = sizeof(T) == 4 && p.ell_ci && p.cptv <= 4;
-  p.g_spmm = resident_grid(spmm_fn<T>(p.cptv, ell), p.smem, true, p.nblk);
+  if (ell) {
+    p.smem_ell = ell_smem_bytes(p.tpr, p.ld);
+    (void)cudaFuncSetAttribute(spmm_fn<T>(p.cptv, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)p.smem_ell);
+  }
+  p.g_spmm = resident_grid(spmm_fn<T>(p.cptv, ell), ell ? p.smem_ell : p.smem, true, p.nblk);
   p.g_resid = resident_grid(resid_fn<T>(p.cptv), p.smem, true, p.nblk);
   p.g_dir = resident_grid(dir_fn<T>(p.cptv), 0, false, 1 << 20);
 }
@@ -1097,8 +1191,8 @@ static int plan_spmm(const CgPlan& p, const T* vals, const T* P, T* Q, double* p
                      int* cnt = nullptr, int freeze = 1) {
   if constexpr (sizeof(T) == 4) {
     if (p.ell_ci && p.cptv <= 4)
-      return launch_spmm_ell(p.cptv, dim3(p.g_spmm), p.tpr, p.smem, st, p.n, p.ell_ci, p.ell_va, p.tail_ptr,
-                             p.tail_ci, p.tail_va, P, Q, p.ld, part, cnt, freeze);
+      return launch_spmm_ell(p.cptv, dim3(p.g_spmm), p.tpr, p.smem_ell, st, p.n, p.ell_ci, p.ell_va, p.tail_ptr,
+                             p.tail_ci, p.tail_va, P, Q, p.ld, part, p.err, cnt, freeze);
   }
   return launch_spmm<T>(p.cptv, dim3(p.g_spmm), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, vals, P, Q, p.ld, part,
                         cnt, freeze);
@@ -1114,6 +1208,7 @@ static CgPlan make_plan(zi_system* S, SolverScratch* w, int cptv, int vecw) {
   p.nblk = w->nblk;
   int rpb = BLOCK / p.tpr;
   p.smem = sizeof(double) * (size_t)rpb * w->ld;
+  p.err = w->cnt + 4;
   p.rowptr = S->rowptr;
   p.colind = S->colind;
   return p;
@@ -1174,13 +1269,17 @@ static int run_cg(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, 
                   cudaGraphExec_t* exec, int* have_chunk, int* ran) {
   ZI_CHECK(get_graph<T>(p, w, vals, X, R, P, Q, chunk, exec, have_chunk));
   int done = 0;
-  int hcnt[3] = {1, 0, 0};
+  int hcnt[5] = {1, 0, 0, 0, 0};
   while (done < maxit) {
     ZI_CUDA(cudaGraphLaunch(*exec, w->stream));
     count_launches(5 * (int64_t)chunk);  // kernel nodes per iteration
     done += chunk;
-    ZI_CUDA(cudaMemcpyAsync(hcnt, w->cnt, 3 * sizeof(int), cudaMemcpyDeviceToHost, w->stream));
+    ZI_CUDA(cudaMemcpyAsync(hcnt, w->cnt, 5 * sizeof(int), cudaMemcpyDeviceToHost, w->stream));
     ZI_CUDA(cudaStreamSynchronize(w->stream));
+    if (hcnt[4]) {
+      ZI_CUDA(cudaMemsetAsync(w->cnt + 4, 0, sizeof(int), w->stream));
+      return device_error_to_status(hcnt[4]);
+    }
     if (hcnt[0] == 0 || hcnt[2] > 0) break;
   }
   *ran = hcnt[1];  // iterations that ran; the rest of the last chunk returned at once
@@ -1230,7 +1329,8 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
     ZI_CHECK(dalloc_n(&w->vec, ld, s));
     ZI_CHECK(dalloc_n(&w->conv, ld, s));
     ZI_CHECK(dalloc_n(&w->iters, ld, s));
-    ZI_CHECK(dalloc_n(&w->cnt, 4, s));
+    ZI_CHECK(dalloc_n(&w->cnt, 5, s));  // [4]: device error word of the CG kernels
+    ZI_CUDA(cudaMemsetAsync(w->cnt, 0, 5 * sizeof(int), s));
     ZI_CHECK(dalloc_n(&w->gamma, ld, s));
     ZI_CHECK(dalloc_n(&w->gamma_prev, ld, s));
     ZI_CHECK(dalloc_n(&w->flag, ld, s));

@@ -167,6 +167,17 @@ def test_lead_field_mixed_precision_within_1e6():
     assert rel(L, Lref) < 1e-6
 
 
+@pytest.mark.parametrize("L,radius", [(100, 0.008), (200, 0.006), (256, 0.005)], ids=["L100", "L200", "L256"])
+def test_lead_field_mixed_precision_wide_layouts(L, radius):
+    """Mixed precision at electrode counts whose FP32 rows split over 26, 52
+    and 64 threads (ld = 104, 208, 256)."""
+    spec = small_shell(L=L, P=50, aniso=True, radius=radius)
+    mesh, s6, gs, dip, pos, q = gpu_head(spec)
+    L_gpu = gs.leadfield(dip, zi.SolverOpts(tol=1e-10, precision=zi.MIXED)).cpu().numpy()
+    om, osys, odip, F = oracle_head(spec)
+    assert rel(L_gpu, O.leadfield(osys, F)) < 1e-6
+
+
 def test_lead_field_ldp_preconditioner():
     spec = small_shell(aniso=False, L=16, P=50)
     mesh, s6, gs, dip, pos, q = gpu_head(spec)
