@@ -39,7 +39,7 @@ WORKLOAD = "three-shell sphere 80/86/92 mm, h=2 mm Kuhn grid (428185 nodes, 2447
            "128 CEM electrodes r=5 mm z=2e-3 Ohm m^2, 20000 dipoles x 3, PCG tol 1e-10"
 # ncu DRAM traffic per launch of the FP32 SpMM on this workload, from the capture
 # summarised in profiles/ (None until taken, or once the kernel source changed).
-SPMM_TRAFFIC = {"source_sha": "352249b46e310d78", "bytes": 247.800064e6 + 188.648704e6}
+SPMM_TRAFFIC = {"source_sha": "c3d2825d867a514f", "bytes": 246.822656e6 + 184.343296e6}
 
 
 def parse():
@@ -180,9 +180,18 @@ def measured_peak_gbs():
 
 
 def spmm_source_sha():
+    """Hash of the source the FP32 ELL SpMM is compiled from: the shared
+    header and zi_pcg.cu up to the end of k_spmm_ell (everything after it --
+    the vector kernels, the batched kernel, the host code -- cannot change
+    the SpMM's code)."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_1811_07717_gb300", "csrc", "zi_pcg.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_1811_07717_gb300", "csrc")
+    with open(os.path.join(csrc, "zi_internal.cuh"), "rb") as f:
+        head = f.read()
+    with open(os.path.join(csrc, "zi_pcg.cu"), "rb") as f:
+        body = f.read()
+    end = body.find(b"// r -= alpha q, with the column partials")
+    return hashlib.sha256(head + (body[:end] if end > 0 else body)).hexdigest()[:16]
 
 
 # ---------------------------------------------------------------------------

@@ -268,18 +268,9 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
 // FP32 inner SpMM on an ELL copy of the matrix: 8 slots per row, the
 // diagonal in slot 0, unused slots with column -1; entries beyond 8 (rows of
 // electrode-patch nodes, anisotropic elements) go to a small CSR tail.  Row
-// i's slots sit at a fixed address, so the loads for the next row are issued
-// while the current row's gathers are in flight (one memory latency per row),
-// and P[i] for the p.q dot is the slot-0 gather.
+// i's slots sit at a fixed address (32 bytes of columns, 32 of values), and
+// P[i] for the p.q dot is the slot-0 gather.
 constexpr int ELL_K = 8;
-
-__device__ __forceinline__ void ell_cols(const int4* __restrict__ ci, int i, int (&j)[ELL_K]) {
-#pragma unroll
-  for (int q = 0; q < ELL_K / 4; ++q) {
-    int4 c = __ldg(ci + i * (ELL_K / 4) + q);
-    j[4 * q + 0] = c.x; j[4 * q + 1] = c.y; j[4 * q + 2] = c.z; j[4 * q + 3] = c.w;
-  }
-}
 
 // The ELL slots of a block's rows are staged in shared memory by the TMA bulk
 // copy engine, a chunk of C = slots * rpb consecutive rows at a time, in a
@@ -1860,6 +1851,13 @@ __device__ __forceinline__ void batch_block_totals(AccT (&acc)[CPTVMAX][W], int 
   }
 }
 
+// Row i's ELL column indices (two 16-byte loads).
+__device__ __forceinline__ void batch_ell_cols(const int4* __restrict__ ci, int i, int (&j)[ELL_K]) {
+  const int4 c0 = __ldg(ci + 2 * i), c1 = __ldg(ci + 2 * i + 1);
+  j[0] = c0.x; j[1] = c0.y; j[2] = c0.z; j[3] = c0.w;
+  j[4] = c1.x; j[5] = c1.y; j[6] = c1.z; j[7] = c1.w;
+}
+
 // One block of the batched solve runs `chunk` CG iterations on its head's
 // rows.  Every row of a head is split over ld / W threads, one 16-byte vector
 // (W columns) each, so the register budget allows four resident blocks per SM.
@@ -1913,7 +1911,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
           int k = 0;
           int i = rw_first(rw);
           int jn[ELL_K];
-          if (i >= 0) ell_cols(eci, i, jn);
+          if (i >= 0) batch_ell_cols(eci, i, jn);
           while (i >= 0) {
             int j[ELL_K];
 #pragma unroll
@@ -1925,7 +1923,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
             for (int u = 0; u < ELL_K; ++u) x[u] = j[u] >= 0 ? ldg_v(Pc + j[u] * nv) : vzero<V>();
             const float4 a0 = __ldg(eva + i * (ELL_K / 4)), a1 = __ldg(eva + i * (ELL_K / 4) + 1);
             const int inext = rw_next(rw, i, k);
-            if (inext >= 0) ell_cols(eci, inext, jn);
+            if (inext >= 0) batch_ell_cols(eci, inext, jn);
             const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             V acc = vzero<V>();
 #pragma unroll
