@@ -49,6 +49,38 @@ template <typename V> __device__ __forceinline__ V vzero();
 template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
+// Packed FP32 pairs (sm_100+ f32x2 arithmetic, IEEE round-to-nearest like
+// the scalar instructions): a float4 is two pairs, so the difference-form
+// update acc += a (x - x0) takes two subtractions and two FMAs.
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// acc += a (x - x0)
+__device__ __forceinline__ void vfma_diff(float4& acc, float a, const float4& x, const float4& x0) {
+  const unsigned long long aa = f2pack(a, a);
+  const unsigned long long lo =
+      f2fma(aa, f2sub(f2pack(x.x, x.y), f2pack(x0.x, x0.y)), f2pack(acc.x, acc.y));
+  const unsigned long long hi =
+      f2fma(aa, f2sub(f2pack(x.z, x.w), f2pack(x0.z, x0.w)), f2pack(acc.z, acc.w));
+  f2unpack(lo, acc.x, acc.y);
+  f2unpack(hi, acc.z, acc.w);
+}
 __device__ __forceinline__ void vfma(double2& acc, double a, const double2& x) {
   acc.x = fma(a, x.x, acc.x);
   acc.y = fma(a, x.y, acc.y);
@@ -397,12 +429,14 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
             x[u][v] = j[u] >= 0 ? ldg_v(Pv + (j[u] * nv + v * tpr)) : vzero<V>();  // n*ld/2 < 2^31 (host-checked)
         const float4 a0 = bv[2 * lr], a1 = bv[2 * lr + 1];
         const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        // difference form: c_i p_i + sum_j a_ij (p_j - p_i); unused slots have a = 0
         V acc[CPTV];
 #pragma unroll
         for (int v = 0; v < CPTV; ++v) {
           acc[v] = vzero<V>();
+          vfma(acc[v], a[0], x[0][v]);
 #pragma unroll
-          for (int u = 0; u < ELL_K; ++u) vfma(acc[v], a[u], x[u][v]);
+          for (int u = 1; u < ELL_K; ++u) vfma_diff(acc[v], a[u], x[u][v], x[0][v]);
         }
         if (tail) {
           const int t0 = __ldg(tail_ptr + i), t1 = __ldg(tail_ptr + i + 1);
@@ -410,7 +444,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
             const int jj = __ldg(tail_ci + t);
             const float aa = __ldg(tail_va + t);
 #pragma unroll
-            for (int v = 0; v < CPTV; ++v) vfma(acc[v], aa, ldg_v(Pv + (jj * nv + v * tpr)));
+            for (int v = 0; v < CPTV; ++v) vfma_diff(acc[v], aa, ldg_v(Pv + (jj * nv + v * tpr)), x[0][v]);
           }
         }
 #pragma unroll
@@ -441,8 +475,9 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
 template <typename T, int CPTV>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
     k_cg_resid(int64_t n, int tpr, int ld, const double* __restrict__ alpha, const T* __restrict__ Q,
-               T* __restrict__ R, const double* __restrict__ dtrue, double* __restrict__ part_rr,
-               double* __restrict__ part_rd, const int* __restrict__ cnt, int freeze) {
+               T* __restrict__ R, const double* __restrict__ dtrue, const double* __restrict__ wrr,
+               double* __restrict__ part_rr, double* __restrict__ part_rd, const int* __restrict__ cnt,
+               int freeze) {
   if (run_stopped(cnt, freeze)) return;
   using V = typename Vec<T>::type;
   constexpr int W = Vec<T>::W;
@@ -468,6 +503,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
     int slot = 0;
     for (int i = rw_first(rw); i >= 0; i = rw_next(rw, i, slot)) {
       const T di = (T)__ldg(dtrue + i);
+      const T wi = wrr ? (T)__ldg(wrr + i) : T(1);
 #pragma unroll
       for (int v = 0; v < CPTV; ++v) {
         const int o = i * nv + c + v * tpr;
@@ -476,7 +512,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
         for (int k = 0; k < W; ++k) {
           T rv = vget(r, k) - al[v][k] * vget(q, k);
           vset(r, k, rv);
-          rr[v][k] += rv * rv;
+          rr[v][k] += wi * rv * rv;
           rd[v][k] += di * rv * rv;
         }
         Rv[o] = r;
@@ -489,11 +525,14 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
   cluster_column_store(stot, ld, part_rd);
 }
 
-// x += alpha p and p = r + beta p in one pass over p.
+// x += alpha p and p = z + beta p in one pass over p, with z = w r (the
+// preconditioned residual of the inner FP32 PCG) or z = r (wz null: CG on the
+// scaled FP64 system).
 template <typename T, int CPTV>
 __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, int tpr, int ld, const double* __restrict__ alpha,
                                                 const double* __restrict__ beta, const T* __restrict__ R,
-                                                T* __restrict__ P, T* __restrict__ X, const int* __restrict__ cnt) {
+                                                const double* __restrict__ wz, T* __restrict__ P,
+                                                T* __restrict__ X, const int* __restrict__ cnt) {
   if (cnt && *(volatile const int*)(cnt + 3)) return;
   using V = typename Vec<T>::type;
   constexpr int W = Vec<T>::W;
@@ -515,6 +554,7 @@ __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, int tpr, int ld, cons
   const RowWalk rw = row_walk(n, rpb, g);
   int slot = 0;
   for (int i = rw_first(rw); i >= 0; i = rw_next(rw, i, slot)) {
+    const T wi = wz ? (T)__ldg(wz + i) : T(1);
 #pragma unroll
     for (int v = 0; v < CPTV; ++v) {
       const int o = i * nv + c + v * tpr;
@@ -522,7 +562,7 @@ __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, int tpr, int ld, cons
 #pragma unroll
       for (int k = 0; k < W; ++k) {
         vset(x, k, vget(x, k) + al[v][k] * vget(p, k));
-        vset(p, k, vget(r, k) + be[v][k] * vget(p, k));
+        vset(p, k, wi * vget(r, k) + be[v][k] * vget(p, k));
       }
       Xv[o] = x;
       Pv[o] = p;
@@ -687,18 +727,26 @@ __global__ void k_count32(int64_t n, const int32_t* __restrict__ rowptr, const i
   }
 }
 
+// The FP32 operator is the unscaled matrix in difference form,
+//   (A p)_i = c_i p_i + sum_{j != i} a_ij (p_j - p_i),   c_i = sum_j a_ij,
+// so v32 holds a_ij off the diagonal and the FP64 row sum c_i on it.  The
+// stiffness part has zero row sums (constants are in its null space), so for
+// the smooth vectors that dominate late CG iterations the differences are
+// small and exact-ish, where the plain form 6 p_i - sum p_j would cancel to a
+// few significant FP32 bits.  Entries the FP32 copy omits (keep32) stay in c_i.
 __global__ void k_fill32(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                          const double* __restrict__ vals, const double* __restrict__ s,
                          const int32_t* __restrict__ diagpos, const int32_t* __restrict__ rowptr32,
                          int32_t* __restrict__ colind32, float* __restrict__ v32) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double rowsum = 0.0;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) rowsum += vals[k];
     int o = rowptr32[i];
     for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
       int32_t j = colind[k];
-      double v = s[i] * vals[k] * s[j];
-      if (keep32(i, j, v, s, vals, diagpos)) {
+      if (keep32(i, j, s[i] * vals[k] * s[j], s, vals, diagpos)) {
         colind32[o] = j;
-        v32[o] = (float)v;
+        v32[o] = (float)(j == (int32_t)i ? rowsum : vals[k]);
         ++o;
       }
     }
@@ -857,13 +905,14 @@ __global__ void k_unscale_out(int64_t n, int ncol, int ld, const double* __restr
   }
 }
 
-// Mixed precision: inner right-hand side r32 = (S r64) / gamma_c and x32 = 0,
-// with column partials of |r32|^2; gamma_c = |r64_c|_2.  On the first phase
-// p32 = r32.  On later phases (reliable update: the FP64 residual replaces
+// Mixed precision: inner right-hand side r32 = r64 / gamma_c and x32 = 0, with
+// column partials of r32.w r32 (w: the PCG preconditioner); gamma_c =
+// |r64_c|_2.  On the first phase p32 = w r32 (the preconditioned residual).
+// On later phases (reliable update: the FP64 residual replaces
 // the recurrence residual) the search direction is kept and rescaled into the
 // new normalisation, p32 *= gamma_prev_c / gamma_c, so CG keeps its
 // conjugate directions instead of restarting.
-__global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ s, const double* __restrict__ R64,
+__global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ w, const double* __restrict__ R64,
                              const double* __restrict__ gamma, const double* __restrict__ gamma_prev, int keep_p,
                              float* __restrict__ r32, float* __restrict__ x32, float* __restrict__ p32,
                              double* __restrict__ part_rr) {
@@ -878,11 +927,11 @@ __global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ s, co
     float ratio = kp ? (float)(gamma_prev[col] * gi) : 0.f;
     for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
       int64_t e = i * ld + col;
-      float r = (float)(s[i] * R64[e] * gi);
+      float r = (float)(R64[e] * gi);
       r32[e] = r;
-      p32[e] = kp ? p32[e] * ratio : r;
+      p32[e] = kp ? p32[e] * ratio : (float)w[i] * r;
       x32[e] = 0.f;
-      rr += (double)r * (double)r;
+      rr += w[i] * (double)r * (double)r;
     }
     sred[g * ld + col] = rr;
   }
@@ -894,14 +943,16 @@ __global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ s, co
   }
 }
 
-// x64 += gamma_c * s_i * x32
-__global__ void k_accumulate(int64_t n, int ld, const double* __restrict__ s, const double* __restrict__ gamma,
-                             const float* __restrict__ x32, double* __restrict__ X64) {
-  int64_t tot = n * (int64_t)ld;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = e / ld;
-    int col = (int)(e % ld);
-    X64[e] += gamma[col] * s[i] * (double)x32[e];
+// x64 += gamma_c * x32 (the inner solve works on the unscaled system); thread
+// (g, col) of a block takes column col of rows g, g + rpb, ...
+__global__ void k_accumulate(int64_t n, int ld, const double* __restrict__ gamma, const float* __restrict__ x32,
+                             double* __restrict__ X64) {
+  const int col = threadIdx.x % ld, rpb = blockDim.x / ld, g = threadIdx.x / ld;
+  if (g >= rpb) return;
+  const double gc = gamma[col];
+  for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
+    const int64_t e = i * ld + col;
+    X64[e] += gc * (double)x32[e];
   }
 }
 
@@ -917,7 +968,7 @@ struct SolverScratch {
   int nblk = 0;
   double* s = nullptr;       // n
   double* dtrue = nullptr;   // n
-  double* ones = nullptr;    // n (stop weights of the inner FP32 solve)
+  double* w32 = nullptr;     // n: s_i^2, the preconditioner of the inner FP32 PCG (unscaled system)
   double* v64 = nullptr;     // nnz scaled FP64
   float* v32 = nullptr;      // nnz32 scaled FP32 values (resolvable entries only)
   int32_t* rowptr32 = nullptr;  // n + 1
@@ -960,7 +1011,7 @@ void solver_scratch_free(zi_system* S) {
   SolverScratch* w = S ? S->solver : nullptr;
   if (!w) return;
   cudaStream_t s = 0;
-  void* ptrs[] = {w->s, w->dtrue, w->ones, w->v64, w->v32, w->rowptr32, w->colind32, w->ell_ci, w->ell_va, w->tail_ptr, w->tail_ci, w->tail_va, w->X, w->R, w->P, w->Q, w->x32, w->r32, w->p32, w->q32,
+  void* ptrs[] = {w->s, w->dtrue, w->w32, w->v64, w->v32, w->rowptr32, w->colind32, w->ell_ci, w->ell_va, w->tail_ptr, w->tail_ci, w->tail_va, w->X, w->R, w->P, w->Q, w->x32, w->r32, w->p32, w->q32,
                   w->part0, w->part1, w->part2, w->rho, w->alpha, w->beta, w->stop2, w->bb, w->vec,
                   w->conv, w->iters, w->cnt, w->gamma, w->gamma_prev, w->flag, w->nact, w->bar, w->gpart};
   for (void* p : ptrs) dfree(p, s);
@@ -1033,13 +1084,13 @@ int launch_spmm_ell(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, 
 
 template <typename T>
 int launch_resid(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, int ld,
-                 const double* alpha, const T* Q, T* R, const double* dtrue, double* prr, double* prd,
-                 const int* cnt, int freeze) {
+                 const double* alpha, const T* Q, T* R, const double* dtrue, const double* wrr, double* prr,
+                 double* prd, const int* cnt, int freeze) {
   switch (cptv) {
-    case 1: k_cg_resid<T, 1><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd, cnt, freeze); break;
-    case 2: k_cg_resid<T, 2><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd, cnt, freeze); break;
-    case 4: k_cg_resid<T, 4><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd, cnt, freeze); break;
-    case 8: k_cg_resid<T, 8><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, prr, prd, cnt, freeze); break;
+    case 1: k_cg_resid<T, 1><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, wrr, prr, prd, cnt, freeze); break;
+    case 2: k_cg_resid<T, 2><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, wrr, prr, prd, cnt, freeze); break;
+    case 4: k_cg_resid<T, 4><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, wrr, prr, prd, cnt, freeze); break;
+    case 8: k_cg_resid<T, 8><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, wrr, prr, prd, cnt, freeze); break;
     default: return set_error(ZI_ERR_ARG, "unsupported column layout");
   }
   ZI_LAUNCH_CHECK();
@@ -1048,12 +1099,12 @@ int launch_resid(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int
 
 template <typename T>
 int launch_dir(int cptv, dim3 grid, int tpr, cudaStream_t st, int64_t n, int ld, const double* alpha,
-               const double* beta, const T* R, T* P, T* X, const int* cnt) {
+               const double* beta, const T* R, const double* wz, T* P, T* X, const int* cnt) {
   switch (cptv) {
-    case 1: k_cg_dir<T, 1><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X, cnt); break;
-    case 2: k_cg_dir<T, 2><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X, cnt); break;
-    case 4: k_cg_dir<T, 4><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X, cnt); break;
-    case 8: k_cg_dir<T, 8><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, P, X, cnt); break;
+    case 1: k_cg_dir<T, 1><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, wz, P, X, cnt); break;
+    case 2: k_cg_dir<T, 2><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, wz, P, X, cnt); break;
+    case 4: k_cg_dir<T, 4><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, wz, P, X, cnt); break;
+    case 8: k_cg_dir<T, 8><<<grid, BLOCK, 0, st>>>(n, tpr, ld, alpha, beta, R, wz, P, X, cnt); break;
     default: return set_error(ZI_ERR_ARG, "unsupported column layout");
   }
   ZI_LAUNCH_CHECK();
@@ -1181,12 +1232,14 @@ template <typename T>
 static int plan_spmm(const CgPlan& p, const T* vals, const T* P, T* Q, double* part, cudaStream_t st,
                      int* cnt = nullptr, int freeze = 1) {
   if constexpr (sizeof(T) == 4) {
-    if (p.ell_ci && p.cptv <= 4)
-      return launch_spmm_ell(p.cptv, dim3(p.g_spmm), p.tpr, p.smem_ell, st, p.n, p.ell_ci, p.ell_va, p.tail_ptr,
-                             p.tail_ci, p.tail_va, P, Q, p.ld, part, p.err, cnt, freeze);
+    // the FP32 operator is stored in difference form, which only the ELL kernel applies
+    if (!p.ell_ci || p.cptv > 4) return set_error(ZI_ERR_ARG, "FP32 SpMM needs the ELL copy");
+    return launch_spmm_ell(p.cptv, dim3(p.g_spmm), p.tpr, p.smem_ell, st, p.n, p.ell_ci, p.ell_va, p.tail_ptr,
+                           p.tail_ci, p.tail_va, P, Q, p.ld, part, p.err, cnt, freeze);
+  } else {
+    return launch_spmm<T>(p.cptv, dim3(p.g_spmm), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, vals, P, Q, p.ld,
+                          part, cnt, freeze);
   }
-  return launch_spmm<T>(p.cptv, dim3(p.g_spmm), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, vals, P, Q, p.ld, part,
-                        cnt, freeze);
 }
 
 static CgPlan make_plan(zi_system* S, SolverScratch* w, int cptv, int vecw) {
@@ -1211,6 +1264,9 @@ static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T
                              cudaStream_t st) {
   ColState cs{w->rho, w->alpha, w->beta, w->stop2, w->conv, w->iters, w->cnt, w->cnt + 1, w->cnt + 2,
               sizeof(T) == sizeof(double) ? 1 : 0};
+  // FP32 inner solve: Jacobi/LDP-preconditioned CG on the unscaled matrix
+  // (z = w r, w = s^2); FP64: CG on the scaled matrix.
+  const double* wpcg = sizeof(T) == 4 ? w->w32 : nullptr;
   // partials per reduction: one per cluster of each kernel's resident grid
   const int ncl_spmm = p.g_spmm / CLUSTER, ncl_resid = p.g_resid / CLUSTER;
   for (int k = 0; k < chunk; ++k) {
@@ -1218,10 +1274,10 @@ static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T
     k_fin_alpha<<<1, FIN_THREADS, 0, st>>>(ncl_spmm, p.ld, p.ncol, w->part0, cs);
     ZI_LAUNCH_CHECK();
     ZI_CHECK(launch_resid<T>(p.cptv, dim3(p.g_resid), p.tpr, p.smem, st, p.n, p.ld, w->alpha, Q, R, w->dtrue,
-                             w->part1, w->part2, w->cnt, cs.freeze));
+                             wpcg, w->part1, w->part2, w->cnt, cs.freeze));
     k_fin_beta<<<1, FIN_THREADS, 0, st>>>(ncl_resid, p.ld, p.ncol, w->part1, w->part2, cs);
     ZI_LAUNCH_CHECK();
-    ZI_CHECK(launch_dir<T>(p.cptv, dim3(p.g_dir), p.tpr, st, p.n, p.ld, w->alpha, w->beta, R, P, X, w->cnt));
+    ZI_CHECK(launch_dir<T>(p.cptv, dim3(p.g_dir), p.tpr, st, p.n, p.ld, w->alpha, w->beta, R, wpcg, P, X, w->cnt));
   }
   return ZI_OK;
 }
@@ -1277,11 +1333,12 @@ static int run_cg(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, 
   return ZI_OK;
 }
 
-// Weights of the inner FP32 solve's stopping test: ones, so the test is on
-// the scaled-space norm |r~32|.
-__global__ void k_ones(int64_t n, double* __restrict__ v) {
+// Preconditioner of the inner FP32 PCG on the unscaled matrix: w = s^2
+// (1/a_ii for Jacobi, 1/sum_j |a_ij| for LDP).  r.w r is then the squared
+// norm of the scaled residual, the quantity the FP64 path tests.
+__global__ void k_square(int64_t n, const double* __restrict__ s, double* __restrict__ w) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = 1.0;
+    w[i] = s[i] * s[i];
 }
 
 static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s) {
@@ -1332,9 +1389,7 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
     ZI_CHECK(dalloc_n(&w->v32, S->nnz, s));
     ZI_CHECK(dalloc_n(&w->rowptr32, S->n + 1, s));
     ZI_CHECK(dalloc_n(&w->colind32, S->nnz, s));
-    ZI_CHECK(dalloc_n(&w->ones, S->n, s));
-    k_ones<<<grid_for(S->n, 256), 256, 0, s>>>(S->n, w->ones);
-    ZI_LAUNCH_CHECK();
+    ZI_CHECK(dalloc_n(&w->w32, S->n, s));
     ZI_CHECK(dalloc_n(&w->x32, nl, s));
     ZI_CHECK(dalloc_n(&w->r32, nl, s));
     ZI_CHECK(dalloc_n(&w->p32, nl, s));
@@ -1428,6 +1483,8 @@ static int prepare_matrices(zi_system* S, const zi_solver_opts* o, cudaStream_t 
     w->precond = o->precond;
   }
   if (mixed && !w->v32_ready) {
+    k_square<<<grid_for(n, 256), 256, 0, st>>>(n, w->s, w->w32);
+    ZI_LAUNCH_CHECK();
     DevTmp<int32_t> cnt;
     ZI_CHECK(cnt.alloc(n, st));
     k_count32<<<grid_for(n, 256), 256, 0, st>>>(n, S->rowptr, S->colind, S->vals, w->s, S->diagpos, cnt.p);
@@ -1570,9 +1627,9 @@ int mixed_phase_begin(HeadRun& h) {
     h.status = set_error(ZI_ERR_NOT_CONVERGED, "mixed-precision refinement missed tol=%g", o->tol);
     return ZI_OK;
   }
-  // inner right-hand side r~32 = S R64 / |R64|, x32 = 0, p32 = r~32 (kept and
+  // inner right-hand side r32 = R64 / |R64|, x32 = 0, p32 = w r32 (kept and
   // rescaled after the first phase)
-  k_prep_inner<<<nblk, BLOCK, smem_init, st>>>(n, ld, w->s, w->R, w->gamma, w->gamma_prev, h.outer > 0 ? 1 : 0,
+  k_prep_inner<<<nblk, BLOCK, smem_init, st>>>(n, ld, w->w32, w->R, w->gamma, w->gamma_prev, h.outer > 0 ? 1 : 0,
                                                w->r32, w->x32, w->p32, w->part0);
   ZI_LAUNCH_CHECK();
   k_init_cols<<<1, FIN_THREADS, 0, st>>>(nblk, ld, ncol, w->part0, nullptr, itol * itol, w->flag, w->rho, w->stop2,
@@ -1599,8 +1656,8 @@ int head_after_inner(HeadRun& h, int ran) {
   for (int c = 0; c < ncol; ++c) h.iters[c] += it[c];
   h.total += ran;
   if (h.mixed) {
-    // X64 += gamma * S * x32 ; R64 = B - A X64
-    k_accumulate<<<grid_for(n * ld, 256), 256, 0, st>>>(n, ld, w->s, w->gamma, w->x32, w->X);
+    // X64 += gamma * x32 ; R64 = B - A X64
+    k_accumulate<<<nblk, BLOCK, 0, st>>>(n, ld, w->gamma, w->x32, w->X);
     ZI_LAUNCH_CHECK();
     ZI_CHECK(launch_residual(h.c64, dim3(nblk), h.p64.tpr, h.p64.smem, st, n, ncol, ld, S->rowptr, S->colind,
                              S->vals, w->X, S->B, w->R, w->part0));
@@ -1690,7 +1747,7 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
     int ran = 0;
     if (h.mixed) {
       double* dtrue_saved = w->dtrue;
-      w->dtrue = w->ones;
+      w->dtrue = w->w32;
       int st2 = run_cg<float>(h.p32, w, w->v32, w->x32, w->r32, w->p32, w->q32, o->maxit - h.total, chunk,
                               &w->graph32, &w->graph_chunk32, &ran);
       w->dtrue = dtrue_saved;
@@ -1733,6 +1790,7 @@ struct BatchHead {
   const float* tail_va;
   T *X, *R, *P, *Q;
   const double* dtrue;
+  const double* wz;  // FP32 heads: the inner PCG preconditioner w (z = w r); FP64 heads: null
   double *rho, *alpha, *beta, *stop2;
   int *conv, *iters, *cnt;
   double *part0, *part1, *part2;     // per-block column partials
@@ -1925,12 +1983,15 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
             const int inext = rw_next(rw, i, k);
             if (inext >= 0) batch_ell_cols(eci, inext, jn);
             const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            // difference form of the FP32 operator (as in k_spmm_ell)
             V acc = vzero<V>();
+            vfma(acc, a[0], x[0]);
 #pragma unroll
-            for (int u = 0; u < ELL_K; ++u) vfma(acc, a[u], x[u]);
+            for (int u = 1; u < ELL_K; ++u) vfma_diff(acc, a[u], x[u], x[0]);
             if (tail) {
               const int t0 = __ldg(H.tail_ptr + i), t1 = __ldg(H.tail_ptr + i + 1);
-              for (int t = t0; t < t1; ++t) vfma(acc, __ldg(H.tail_va + t), ldg_v(Pc + __ldg(H.tail_ci + t) * nv));
+              for (int t = t0; t < t1; ++t)
+                vfma_diff(acc, __ldg(H.tail_va + t), ldg_v(Pc + __ldg(H.tail_ci + t) * nv), x[0]);
             }
             Qc[i * nv] = acc;
 #pragma unroll
@@ -1939,7 +2000,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
           }
         }
       }
-      if (!ell) {
+      if (sizeof(T) == 8 && !ell) {  // FP32 heads always carry the ELL copy (host-checked)
         const int32_t* rowptr = H.rowptr;
         const int32_t* colind = H.colind;
         const T* vals = H.vals;
@@ -1998,13 +2059,14 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
       int k = 0;
       for (int i = rw_first(rw); i >= 0; i = rw_next(rw, i, k)) {
         const T di = (T)__ldg(H.dtrue + i);
+        const T wi = H.wz ? (T)__ldg(H.wz + i) : T(1);
         const V q = Qc[i * nv];
         V r = Rc[i * nv];
 #pragma unroll
         for (int u = 0; u < W; ++u) {
           const T rv = vget(r, u) - al[u] * vget(q, u);
           vset(r, u, rv);
-          rr[0][u] += rv * rv;
+          rr[0][u] += wi * rv * rv;
           rd[0][u] += di * rv * rv;
         }
         Rc[i * nv] = r;
@@ -2068,12 +2130,13 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
       }
       int k = 0;
       for (int i = rw_first(rw); i >= 0; i = rw_next(rw, i, k)) {
+        const T wi = H.wz ? (T)__ldg(H.wz + i) : T(1);
         const V r = Rc[i * nv];
         V p = Pc[i * nv], x = Xc[i * nv];
 #pragma unroll
         for (int u = 0; u < W; ++u) {
           vset(x, u, vget(x, u) + al[u] * vget(p, u));
-          vset(p, u, vget(r, u) + be[u] * vget(p, u));
+          vset(p, u, wi * vget(r, u) + be[u] * vget(p, u));
         }
         Xc[i * nv] = x;
         Pc[i * nv] = p;
@@ -2150,6 +2213,7 @@ static int run_batched_chunk(std::vector<HeadRun*>& act, int chunk, cudaStream_t
   for (int k = 0; k < nh; ++k) {
     HeadRun* h = act[k];
     SolverScratch* w = h->S->solver;
+    if (sizeof(T) == 4 && !w->ell_ci) return set_error(ZI_ERR_ARG, "FP32 batched head without its ELL copy");
     BatchHead<T>& b = hh[k];
     b.n = h->S->n;
     b.ld = w->ld;
@@ -2176,13 +2240,15 @@ static int run_batched_chunk(std::vector<HeadRun*>& act, int chunk, cudaStream_t
       b.tail_ci = w->tail_ci;
       b.tail_va = w->tail_va;
       b.X = w->x32; b.R = w->r32; b.P = w->p32; b.Q = w->q32;
-      b.dtrue = w->ones;
+      b.dtrue = w->w32;
+      b.wz = w->w32;
     } else {
       b.rowptr = h->S->rowptr;
       b.colind = h->S->colind;
       b.vals = w->v64;
       b.X = w->X; b.R = w->R; b.P = w->P; b.Q = w->Q;
       b.dtrue = w->dtrue;
+      b.wz = nullptr;
     }
     b.rho = w->rho; b.alpha = w->alpha; b.beta = w->beta; b.stop2 = w->stop2;
     b.conv = w->conv; b.iters = w->iters; b.cnt = w->cnt;
