@@ -187,7 +187,7 @@ typedef struct zi_solver_opts {
   int32_t maxit;      /* bound on inner CG iterations in total per solve */
   int32_t precond;    /* ZI_PRECOND_JACOBI or ZI_PRECOND_LDP */
   int32_t precision;  /* ZI_FP64 or ZI_MIXED */
-  double inner_tol;   /* ZI_MIXED: FP32 residual reduction between FP64 reliable updates (0 = default 0.1) */
+  double inner_tol;   /* ZI_MIXED: FP32 residual reduction between FP64 reliable updates (0 = default 0.05) */
   int32_t max_outer;  /* ZI_MIXED: bound on refinement steps (0 = default 30) */
   int32_t check_every;/* iterations between convergence read-backs (0 = default) */
 } zi_solver_opts;

@@ -916,43 +916,71 @@ __global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ w, co
                              const double* __restrict__ gamma, const double* __restrict__ gamma_prev, int keep_p,
                              float* __restrict__ r32, float* __restrict__ x32, float* __restrict__ p32,
                              double* __restrict__ part_rr) {
+  // thread (g, c) handles columns 4c .. 4c + 3 of rows g, g + rpb, ... (ld is a multiple of 4)
   extern __shared__ double sred[];
-  const int col = threadIdx.x % ld;
-  const int rpb = blockDim.x / ld;
-  const int g = threadIdx.x / ld;
-  double rr = 0.0;
+  const int nq = ld / 4;
+  const int c = threadIdx.x % nq, g = threadIdx.x / nq, rpb = blockDim.x / nq;
+  double rr[4] = {0.0, 0.0, 0.0, 0.0};
   if (g < rpb) {
-    double gi = gamma[col] > 0.0 ? 1.0 / gamma[col] : 0.0;
-    bool kp = keep_p && gamma[col] > 0.0 && gamma_prev[col] > 0.0;
-    float ratio = kp ? (float)(gamma_prev[col] * gi) : 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
-      int64_t e = i * ld + col;
-      float r = (float)(R64[e] * gi);
-      r32[e] = r;
-      p32[e] = kp ? p32[e] * ratio : (float)w[i] * r;
-      x32[e] = 0.f;
-      rr += w[i] * (double)r * (double)r;
+    double gi[4];
+    float ratio[4];
+    bool kp[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int col = 4 * c + k;
+      gi[k] = gamma[col] > 0.0 ? 1.0 / gamma[col] : 0.0;
+      kp[k] = keep_p && gamma[col] > 0.0 && gamma_prev[col] > 0.0;
+      ratio[k] = kp[k] ? (float)(gamma_prev[col] * gi[k]) : 0.f;
     }
-    sred[g * ld + col] = rr;
+    for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
+      const int64_t e = i * ld + 4 * c;
+      const double2 ra = *reinterpret_cast<const double2*>(R64 + e);
+      const double2 rb = *reinterpret_cast<const double2*>(R64 + e + 2);
+      const double r64[4] = {ra.x, ra.y, rb.x, rb.y};
+      const double wi = w[i];
+      float4 pold = keep_p ? *reinterpret_cast<const float4*>(p32 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float po[4] = {pold.x, pold.y, pold.z, pold.w};
+      float r[4], pn[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        r[k] = (float)(r64[k] * gi[k]);
+        pn[k] = kp[k] ? po[k] * ratio[k] : (float)wi * r[k];
+        rr[k] += wi * (double)r[k] * (double)r[k];
+      }
+      *reinterpret_cast<float4*>(r32 + e) = make_float4(r[0], r[1], r[2], r[3]);
+      *reinterpret_cast<float4*>(p32 + e) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+      *reinterpret_cast<float4*>(x32 + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sred[g * ld + 4 * c + k] = rr[k];
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+  for (int col = threadIdx.x; col < ld; col += blockDim.x) {
     double t = 0.0;
-    for (int gg = 0; gg < rpb; ++gg) t += sred[gg * ld + c];
-    part_rr[(int64_t)blockIdx.x * ld + c] = t;
+    for (int gg = 0; gg < rpb; ++gg) t += sred[gg * ld + col];
+    part_rr[(int64_t)blockIdx.x * ld + col] = t;
   }
 }
 
 // x64 += gamma_c * x32 (the inner solve works on the unscaled system); thread
-// (g, col) of a block takes column col of rows g, g + rpb, ...
+// (g, c) of a block takes columns 4c .. 4c + 3 of rows g, g + rpb, ...
 __global__ void k_accumulate(int64_t n, int ld, const double* __restrict__ gamma, const float* __restrict__ x32,
                              double* __restrict__ X64) {
-  const int col = threadIdx.x % ld, rpb = blockDim.x / ld, g = threadIdx.x / ld;
+  const int nq = ld / 4;
+  const int c = threadIdx.x % nq, g = threadIdx.x / nq, rpb = blockDim.x / nq;
   if (g >= rpb) return;
-  const double gc = gamma[col];
+  const double g0 = gamma[4 * c], g1 = gamma[4 * c + 1], g2 = gamma[4 * c + 2], g3 = gamma[4 * c + 3];
   for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
-    const int64_t e = i * ld + col;
-    X64[e] += gc * (double)x32[e];
+    const int64_t e = i * ld + 4 * c;
+    const float4 xv = *reinterpret_cast<const float4*>(x32 + e);
+    double2* X = reinterpret_cast<double2*>(X64 + e);
+    double2 a = X[0], b = X[1];
+    a.x += g0 * (double)xv.x;
+    a.y += g1 * (double)xv.y;
+    b.x += g2 * (double)xv.z;
+    b.y += g3 * (double)xv.w;
+    X[0] = a;
+    X[1] = b;
   }
 }
 
@@ -1604,7 +1632,7 @@ int mixed_phase_begin(HeadRun& h) {
   const int64_t n = S->n;
   const int ld = w->ld, ncol = S->n_rhs, nblk = w->nblk;
   const double tol2 = o->tol * o->tol;
-  const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-1;
+  const double itol = o->inner_tol > 0 ? o->inner_tol : 5e-2;
   const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
   const size_t smem_init = sizeof(double) * (size_t)(BLOCK / ld) * ld;
   ZI_CUDA(cudaMemcpyAsync(w->gamma_prev, w->gamma, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st));
@@ -1629,7 +1657,8 @@ int mixed_phase_begin(HeadRun& h) {
   }
   // inner right-hand side r32 = R64 / |R64|, x32 = 0, p32 = w r32 (kept and
   // rescaled after the first phase)
-  k_prep_inner<<<nblk, BLOCK, smem_init, st>>>(n, ld, w->w32, w->R, w->gamma, w->gamma_prev, h.outer > 0 ? 1 : 0,
+  const size_t smem_prep = sizeof(double) * (size_t)(BLOCK / (ld / 4)) * ld;  // four columns per thread
+  k_prep_inner<<<nblk, BLOCK, smem_prep, st>>>(n, ld, w->w32, w->R, w->gamma, w->gamma_prev, h.outer > 0 ? 1 : 0,
                                                w->r32, w->x32, w->p32, w->part0);
   ZI_LAUNCH_CHECK();
   k_init_cols<<<1, FIN_THREADS, 0, st>>>(nblk, ld, ncol, w->part0, nullptr, itol * itol, w->flag, w->rho, w->stop2,
@@ -2404,7 +2433,7 @@ extern "C" void zi_solver_opts_default(zi_solver_opts* o) {
   o->maxit = 100000;
   o->precond = ZI_PRECOND_JACOBI;
   o->precision = ZI_FP64;
-  o->inner_tol = 1e-1;
+  o->inner_tol = 5e-2;
   o->max_outer = 30;
   o->check_every = 25;
 }

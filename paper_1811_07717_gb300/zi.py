@@ -160,7 +160,7 @@ class SolverOpts:
     maxit: int = 100000
     precond: int = PRECOND_JACOBI
     precision: int = FP64
-    inner_tol: float = 1e-1
+    inner_tol: float = 5e-2
     max_outer: int = 30
     check_every: int = 25
 
