@@ -98,6 +98,54 @@ def oracle_once() -> float:
     return float(r.stdout.strip().splitlines()[-1])
 
 
+def cpu_pcg_once() -> dict:
+    """The CPU block PCG baseline (oracle/cpu_pcg.c: the same Jacobi PCG,
+    FP64, OpenMP over all host cores) on the oracle sample's matrix, in a
+    fresh process: seconds, iterations and threads of one transfer solve."""
+    code = ("import sys,time,os,json; sys.path.insert(0, %r)\n"
+            "from oracle import zi_oracle as O, cpu_pcg\n"
+            "from paper_1811_07717_gb300 import workloads as W\n"
+            "spec = W.three_shell(%r, %d, 10, seed=2)\n"
+            "mesh = O.mesh_from_grid(spec.h, spec.radii)\n"
+            "s6 = W.conductivity(spec, mesh['nodes'], mesh['tets'], mesh['labels'])\n"
+            "c, z = W.electrode_inputs(spec)\n"
+            "S = O.System(mesh, s6, c, spec.electrode_model, radius=spec.electrode_radius, z=z)\n"
+            "th = len(os.sched_getaffinity(0))\n"
+            "cpu_pcg.block_pcg(S.A, S.B, tol=1e-10, maxit=3, threads=th)\n"
+            "t = time.perf_counter(); T, it, k = cpu_pcg.block_pcg(S.A, S.B, tol=1e-10, threads=th)\n"
+            "print(json.dumps({'s': time.perf_counter() - t, 'iterations': int(k), 'threads': th}))\n"
+            % (ROOT, ORACLE_SAMPLE["h"], ORACLE_SAMPLE["electrodes"]))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("cpu PCG sample failed: " + r.stderr[-500:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def gpu_fp64_same_sample() -> dict:
+    """The GPU FP64 transfer solve of the CPU PCG's sample (same head, same
+    tolerance), for the per-iteration comparison."""
+    import torch
+    from paper_1811_07717_gb300 import workloads as W
+    from paper_1811_07717_gb300 import zi
+    spec = W.three_shell(ORACLE_SAMPLE["h"], ORACLE_SAMPLE["electrodes"], 10, seed=2)
+    mesh = zi.mesh_from_grid(spec.h, spec.radii)
+    s6 = W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(),
+                        mesh["labels"].cpu().numpy())
+    centres, z = W.electrode_inputs(spec)
+    system = zi.System(mesh["nodes"], mesh["tets"], s6, mesh["bfaces"], centres, model="cem", z=z,
+                       radius=spec.electrode_radius)
+    opts = zi.SolverOpts(tol=1e-10)
+    system.transfer(opts, want_T=False)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    _, it, _ = system.transfer(opts, want_T=False)
+    t1.record()
+    torch.cuda.synchronize()
+    system.close()
+    return {"s": t0.elapsed_time(t1) / 1e3, "iterations": int(it.max())}
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -371,6 +419,18 @@ def main():
             cpu = {"value": cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE_TEXT}
         except Exception as ex:  # reported, never silently replaced
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %s" % ex}
+        try:
+            c = cpu_pcg_once()
+            g = gpu_fp64_same_sample()
+            extra["cpu_pcg"] = {
+                "kind": "CPU block PCG, FP64, Jacobi, OpenMP (oracle/cpu_pcg.c)", "threads": c["threads"],
+                "sample": "transfer solve T = A^-1 B of the h=4 mm head (56235 nodes, 128 CEM electrodes), "
+                          "tol 1e-10",
+                "s": c["s"], "iterations": c["iterations"], "s_per_iteration": c["s"] / max(1, c["iterations"]),
+                "gpu_fp64_s": g["s"], "gpu_fp64_iterations": g["iterations"],
+                "gpu_fp64_s_per_iteration": g["s"] / max(1, g["iterations"])}
+        except Exception as ex:
+            extra["cpu_pcg"] = {"failed": str(ex)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": sec_mixed, "unit": UNIT, "n_gpus": world, "steps": args.steps,

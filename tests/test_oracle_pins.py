@@ -510,3 +510,29 @@ def test_pattern_is_the_mesh_graph_whatever_the_values():
     rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
     got = set(zip(rows.tolist(), A.indices.tolist()))
     assert got == pairs
+
+
+# --------------------------------------------------------------------------
+# CPU block PCG baseline (Sec. 2.3.1 iteration) against the direct solve
+# --------------------------------------------------------------------------
+
+def test_cpu_block_pcg_matches_direct_solve():
+    from oracle import cpu_pcg
+    spec = W.three_shell(0.006, 16, 10, seed=21, electrode_radius=0.009)
+    mesh = O.mesh_from_grid(spec.h, spec.radii)
+    s6 = W.conductivity(spec, mesh["nodes"], mesh["tets"], mesh["labels"])
+    centres, z = W.electrode_inputs(spec)
+    system = O.System(mesh, s6, centres, spec.electrode_model, radius=spec.electrode_radius, z=z)
+    T_direct = system.transfer()
+    counts = set()
+    for precond in (0, 1):
+        for threads in (1, 3):
+            T, iters, k = cpu_pcg.block_pcg(system.A, system.B, tol=1e-12, precond=precond, threads=threads)
+            # |T - T*| <= kappa-scaled residual; the residual itself is at the stop test
+            assert np.linalg.norm(T - T_direct) <= 1e-9 * np.linalg.norm(T_direct)
+            res = np.linalg.norm(system.A @ T - system.B, axis=0) / np.linalg.norm(system.B, axis=0)
+            assert np.all(res <= 1e-12 * (1 + 1e-6))
+            assert k == iters.max() and k > 10
+            counts.add((precond, k))
+    # the thread split changes only the summation order of the dots
+    assert len({k for _, k in counts}) <= 2
