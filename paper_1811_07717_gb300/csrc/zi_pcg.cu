@@ -686,15 +686,43 @@ __global__ void k_scale(int64_t n, int precond, const int32_t* __restrict__ rowp
   }
 }
 
-__global__ void k_scaled_values(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                                const double* __restrict__ vals, const double* __restrict__ s,
-                                double* __restrict__ v64, float* __restrict__ v32) {
+// The FP64 solver matrices drop the entries of the mesh-graph pattern that
+// are assembly rounding noise: |a_ij| <= 2^-40 sqrt(|a_ii a_jj|).  On an
+// isotropic Kuhn grid the diagonal-edge couplings are exactly zero in the FE
+// matrix and come out of the element sums at about 1e-16 of the diagonal;
+// genuine couplings are above 1e-8 of it (anisotropic elements included), so
+// the cut removes only noise below the rounding error every assembled entry
+// carries anyway -- and about half of the FP64 FMAs of every product.
+__device__ __forceinline__ bool keep64(int64_t i, int32_t j, double v, const double* vals, const int32_t* diagpos) {
+  if (j == (int32_t)i) return true;
+  const int di = diagpos[i], dj = diagpos[j];
+  const double aii = di >= 0 ? fabs(vals[di]) : 1.0, ajj = dj >= 0 ? fabs(vals[dj]) : 1.0;
+  return fabs(v) > 9.094947017729282e-13 * sqrt(aii * ajj);  // 2^-40
+}
+__global__ void k_count_nonzero(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                const double* __restrict__ vals, const int32_t* __restrict__ diagpos,
+                                int32_t* __restrict__ cnt) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double si = s[i];
+    int c = 0;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) c += keep64(i, colind[k], vals[k], vals, diagpos) ? 1 : 0;
+    cnt[i] = c;
+  }
+}
+__global__ void k_fill_nonzero(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                               const double* __restrict__ vals, const int32_t* __restrict__ diagpos,
+                               const double* __restrict__ s, const int32_t* __restrict__ rowptrc,
+                               int32_t* __restrict__ colindc, double* __restrict__ valsc, double* __restrict__ v64) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double si = s[i];
+    int o = rowptrc[i];
     for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-      double v = si * vals[k] * s[colind[k]];
-      if (v64) v64[k] = v;
-      if (v32) v32[k] = (float)v;
+      const int32_t j = colind[k];
+      if (keep64(i, j, vals[k], vals, diagpos)) {
+        colindc[o] = j;
+        valsc[o] = vals[k];
+        v64[o] = si * vals[k] * s[j];
+        ++o;
+      }
     }
   }
 }
@@ -997,7 +1025,11 @@ struct SolverScratch {
   double* s = nullptr;       // n
   double* dtrue = nullptr;   // n
   double* w32 = nullptr;     // n: s_i^2, the preconditioner of the inner FP32 PCG (unscaled system)
-  double* v64 = nullptr;     // nnz scaled FP64
+  double* v64 = nullptr;     // nnzc scaled FP64 values on the compacted pattern
+  int32_t* rowptrc = nullptr;  // n + 1: A's pattern without its rounding-noise entries (keep64)
+  int32_t* colindc = nullptr;  // nnzc
+  double* valsc = nullptr;     // nnzc: A's (unscaled) values on that pattern
+  int64_t nnzc = 0;
   float* v32 = nullptr;      // nnz32 scaled FP32 values (resolvable entries only)
   int32_t* rowptr32 = nullptr;  // n + 1
   int32_t* colind32 = nullptr;  // nnz32
@@ -1039,7 +1071,7 @@ void solver_scratch_free(zi_system* S) {
   SolverScratch* w = S ? S->solver : nullptr;
   if (!w) return;
   cudaStream_t s = 0;
-  void* ptrs[] = {w->s, w->dtrue, w->w32, w->v64, w->v32, w->rowptr32, w->colind32, w->ell_ci, w->ell_va, w->tail_ptr, w->tail_ci, w->tail_va, w->X, w->R, w->P, w->Q, w->x32, w->r32, w->p32, w->q32,
+  void* ptrs[] = {w->s, w->dtrue, w->w32, w->v64, w->rowptrc, w->colindc, w->valsc, w->v32, w->rowptr32, w->colind32, w->ell_ci, w->ell_va, w->tail_ptr, w->tail_ci, w->tail_va, w->X, w->R, w->P, w->Q, w->x32, w->r32, w->p32, w->q32,
                   w->part0, w->part1, w->part2, w->rho, w->alpha, w->beta, w->stop2, w->bb, w->vec,
                   w->conv, w->iters, w->cnt, w->gamma, w->gamma_prev, w->flag, w->nact, w->bar, w->gpart};
   for (void* p : ptrs) dfree(p, s);
@@ -1281,8 +1313,8 @@ static CgPlan make_plan(zi_system* S, SolverScratch* w, int cptv, int vecw) {
   int rpb = BLOCK / p.tpr;
   p.smem = sizeof(double) * (size_t)rpb * w->ld;
   p.err = w->cnt + 4;
-  p.rowptr = S->rowptr;
-  p.colind = S->colind;
+  p.rowptr = w->rowptrc;
+  p.colind = w->colindc;
   return p;
 }
 
@@ -1390,6 +1422,9 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
     ZI_CHECK(dalloc_n(&w->s, S->n, s));
     ZI_CHECK(dalloc_n(&w->dtrue, S->n, s));
     ZI_CHECK(dalloc_n(&w->v64, S->nnz, s));
+    ZI_CHECK(dalloc_n(&w->rowptrc, S->n + 1, s));
+    ZI_CHECK(dalloc_n(&w->colindc, S->nnz, s));
+    ZI_CHECK(dalloc_n(&w->valsc, S->nnz, s));
     ZI_CHECK(dalloc_n(&w->X, nl, s));
     ZI_CHECK(dalloc_n(&w->R, nl, s));
     ZI_CHECK(dalloc_n(&w->P, nl, s));
@@ -1504,8 +1539,19 @@ static int prepare_matrices(zi_system* S, const zi_solver_opts* o, cudaStream_t 
     k_scale<<<grid_for(n, 256), 256, 0, st>>>(n, o->precond, S->rowptr, S->colind, S->vals, S->diagpos, w->s,
                                               w->dtrue);
     ZI_LAUNCH_CHECK();
-    k_scaled_values<<<grid_for(n, 256), 256, 0, st>>>(n, S->rowptr, S->colind, S->vals, w->s, w->v64, nullptr);
+    DevTmp<int32_t> cnt;
+    ZI_CHECK(cnt.alloc(n, st));
+    k_count_nonzero<<<grid_for(n, 256), 256, 0, st>>>(n, S->rowptr, S->colind, S->vals, S->diagpos, cnt.p);
     ZI_LAUNCH_CHECK();
+    ZI_CHECK(exclusive_scan_i32(cnt.p, w->rowptrc, n, &w->nnzc, st));
+    k_fill_nonzero<<<grid_for(n, 256), 256, 0, st>>>(n, S->rowptr, S->colind, S->vals, S->diagpos, w->s, w->rowptrc,
+                                                     w->colindc, w->valsc, w->v64);
+    ZI_LAUNCH_CHECK();
+    if (w->graph64) {  // a captured graph names the previous pattern's row pointers
+      cudaGraphExecDestroy(w->graph64);
+      w->graph64 = nullptr;
+      w->graph_chunk64 = 0;
+    }
     w->values_ready = true;
     w->v32_ready = false;
     w->precond = o->precond;
@@ -1613,7 +1659,7 @@ int head_begin(HeadRun& h) {
   }
   // mixed: FP64 outer X64 (original space, w->X) = 0, R64 = B; |b|^2 per column
   ZI_CUDA(cudaMemsetAsync(w->X, 0, sizeof(double) * n * ld, st));
-  ZI_CHECK(launch_residual(c64, dim3(nblk), h.p64.tpr, h.p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
+  ZI_CHECK(launch_residual(c64, dim3(nblk), h.p64.tpr, h.p64.smem, st, n, ncol, ld, w->rowptrc, w->colindc, w->valsc,
                            w->X, S->B, w->R, w->part0));
   k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part0, w->bb);
   ZI_LAUNCH_CHECK();
@@ -1688,8 +1734,8 @@ int head_after_inner(HeadRun& h, int ran) {
     // X64 += gamma * x32 ; R64 = B - A X64
     k_accumulate<<<nblk, BLOCK, 0, st>>>(n, ld, w->gamma, w->x32, w->X);
     ZI_LAUNCH_CHECK();
-    ZI_CHECK(launch_residual(h.c64, dim3(nblk), h.p64.tpr, h.p64.smem, st, n, ncol, ld, S->rowptr, S->colind,
-                             S->vals, w->X, S->B, w->R, w->part0));
+    ZI_CHECK(launch_residual(h.c64, dim3(nblk), h.p64.tpr, h.p64.smem, st, n, ncol, ld, w->rowptrc, w->colindc,
+                             w->valsc, w->X, S->B, w->R, w->part0));
     k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part0, w->vec);
     ZI_LAUNCH_CHECK();
     return mixed_phase_begin(h);
@@ -1697,7 +1743,7 @@ int head_after_inner(HeadRun& h, int ran) {
   // true residual in the original space: R0 = B - A (S x~)
   k_unscale_out<<<grid_for(n * ld, 256), 256, 0, st>>>(n, ncol, ld, w->s, w->X, w->Q, nullptr);
   ZI_LAUNCH_CHECK();
-  ZI_CHECK(launch_residual(h.c64, dim3(nblk), h.p64.tpr, h.p64.smem, st, n, ncol, ld, S->rowptr, S->colind, S->vals,
+  ZI_CHECK(launch_residual(h.c64, dim3(nblk), h.p64.tpr, h.p64.smem, st, n, ncol, ld, w->rowptrc, w->colindc, w->valsc,
                            w->Q, S->B, w->P, w->part0));
   k_sum_partials<<<1, FIN_THREADS, 0, st>>>(nblk, ld, w->part0, w->vec);
   ZI_LAUNCH_CHECK();
@@ -2272,8 +2318,8 @@ static int run_batched_chunk(std::vector<HeadRun*>& act, int chunk, cudaStream_t
       b.dtrue = w->w32;
       b.wz = w->w32;
     } else {
-      b.rowptr = h->S->rowptr;
-      b.colind = h->S->colind;
+      b.rowptr = w->rowptrc;
+      b.colind = w->colindc;
       b.vals = w->v64;
       b.X = w->X; b.R = w->R; b.P = w->P; b.Q = w->Q;
       b.dtrue = w->dtrue;
@@ -2530,7 +2576,7 @@ extern "C" int zi_time_spmm(zi_system* S, int precision, int reps, double* ms_pe
     // matrix bytes as stored: ELL slots (column + value) or CSR entries plus row pointers
     double mat = (f32 && w->ell_ci)
                      ? (double)S->n * ELL_K * 8.0 + (w->tail_ptr ? 4.0 * (S->n + 1) + 8.0 * w->ntail : 0.0)
-                     : (double)(f32 ? w->nnz32 : S->nnz) * (w_ + 4.0) + 4.0 * (double)(S->n + 1);
+                     : (double)(f32 ? w->nnz32 : w->nnzc) * (w_ + 4.0) + 4.0 * (double)(S->n + 1);
     *bytes_per_launch = mat +
                         2.0 * w_ * (double)S->n * (double)S->n_rhs;
   }
