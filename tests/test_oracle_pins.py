@@ -536,3 +536,26 @@ def test_cpu_block_pcg_matches_direct_solve():
             counts.add((precond, k))
     # the thread split changes only the summation order of the dots
     assert len({k for _, k in counts}) <= 2
+
+
+def test_assembled_couplings_are_noise_or_genuine():
+    """The solver copies drop couplings below 2^-40 sqrt(a_ii a_jj) as assembly
+    noise (FP64) and below 2^-24 (FP32).  That is safe because the assembled
+    off-diagonal entries fall into two separated groups: the exact zeros of the
+    Kuhn diagonal edges (isotropic elements), which come out at rounding level,
+    and genuine couplings far above both cuts -- isotropic and anisotropic
+    heads alike."""
+    for aniso in (None, (0.00132, 0.0132)):
+        spec = W.three_shell(0.006, 16, 10, seed=2, skull_aniso=aniso)
+        mesh = O.mesh_from_grid(spec.h, spec.radii)
+        s6 = W.conductivity(spec, mesh["nodes"], mesh["tets"], mesh["labels"])
+        centres, z = W.electrode_inputs(spec)
+        system = O.System(mesh, s6, centres, spec.electrode_model, radius=spec.electrode_radius, z=z)
+        A = system.A.tocoo()
+        d = np.abs(system.A.diagonal())
+        off = A.row != A.col
+        rel = np.abs(A.data[off]) / np.sqrt(d[A.row[off]] * d[A.col[off]])
+        noise = rel <= 2.0 ** -40
+        assert noise.sum() > 0.3 * off.sum()            # the diagonal edges are there
+        assert np.all(rel[noise] < 1e-14)               # and at rounding level
+        assert np.all(rel[~noise] > 2.0 ** -24)         # everything else survives both cuts
