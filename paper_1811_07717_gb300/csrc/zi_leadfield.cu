@@ -69,17 +69,48 @@ __global__ void k_source_apply(int64_t P, const int32_t* __restrict__ dip_tet, i
 }
 
 // S[k][l] = C_k delta_kl - sum over patch nodes i (ascending) of B[i][k] T[i][l].
-__global__ void k_schur(int L, int64_t np_, const int32_t* __restrict__ pn, const double* __restrict__ B,
-                        const double* __restrict__ T, const double* __restrict__ C, double* __restrict__ S) {
+// S = C - B^T T over the patch nodes (App. A.2).  Column k of B is nonzero
+// only on electrode k's patch nodes, so block k first compacts, in node
+// order, the patch nodes with b_ik != 0 (a ballot per warp, warp offsets in
+// shared memory) and then sums over that short list; the FMA chain is the
+// one over all patch nodes minus its zero terms.  Thread l owns column l
+// (L <= blockDim.x).
+__global__ void __launch_bounds__(256) k_schur(int L, int64_t np_, const int32_t* __restrict__ pn,
+                                               const double* __restrict__ B, const double* __restrict__ T,
+                                               const double* __restrict__ C, double* __restrict__ S) {
   const int k = blockIdx.x;
-  for (int l = threadIdx.x; l < L; l += blockDim.x) {
-    double s = 0.0;
-    for (int64_t q = 0; q < np_; ++q) {
-      int64_t i = pn[q];
-      s += B[i * L + k] * T[i * L + l];
+  __shared__ int32_t nodes[256];
+  __shared__ double bval[256];
+  __shared__ int wcnt[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double s = 0.0;
+  for (int64_t base = 0; base < np_; base += blockDim.x) {
+    const int64_t q = base + threadIdx.x;
+    int32_t i = -1;
+    double b = 0.0;
+    if (q < np_) {
+      i = pn[q];
+      b = B[(int64_t)i * L + k];
     }
-    S[(int64_t)k * L + l] = (k == l ? C[k] : 0.0) - s;
+    const unsigned m = __ballot_sync(0xffffffffu, b != 0.0);
+    if (lane == 0) wcnt[w] = __popc(m);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) {
+      if (ww < w) off += wcnt[ww];
+      tot += wcnt[ww];
+    }
+    if (b != 0.0) {
+      const int pos = off + __popc(m & ((1u << lane) - 1u));
+      nodes[pos] = i;
+      bval[pos] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x < L)
+      for (int t = 0; t < tot; ++t) s += bval[t] * T[(int64_t)nodes[t] * L + threadIdx.x];
+    __syncthreads();
   }
+  if (threadIdx.x < L) S[(int64_t)k * L + threadIdx.x] = (k == (int)threadIdx.x ? C[k] : 0.0) - s;
 }
 
 // Single block: Cholesky factor of the SPD L x L matrix A (in place, lower),
@@ -119,17 +150,30 @@ __global__ void __launch_bounds__(1024) k_chol_inverse(int L, double* __restrict
     if (threadIdx.x == 0) atomicOr(err, DEV_ERR_NOT_SPD);
     return;
   }
-  // Xout = A^-1: column c solves (G G^T) x = e_c, one thread per column
-  for (int c = threadIdx.x; c < L; c += blockDim.x) {
+  // Xout = A^-1: column c solves (G G^T) x = e_c.  A group of gs lanes of one
+  // warp (gs = the largest power of two <= min(32, blockDim / L)) shares a
+  // column: lane `sub` of the group sums the terms k = sub (mod gs) of every
+  // substitution step, the group adds them with shuffles, and lane 0 writes
+  // the new entry, which __syncwarp makes visible to the group.
+  int gs = 1;
+  while (gs * 2 <= 32 && gs * 2 * L <= (int)blockDim.x) gs *= 2;
+  const int sub = threadIdx.x % gs, ngroups = blockDim.x / gs;
+  for (int c0 = threadIdx.x / gs; c0 - (int)(threadIdx.x / gs) < L; c0 += ngroups) {
+    const bool live = c0 < L;   // idle groups run the loop too (shuffle partners), writing nothing
+    const int c = live ? c0 : L - 1;
     for (int i = 0; i < L; ++i) {  // forward: G y = e_c, y stored in Xout[:, c]
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) s -= A[(int64_t)i * L + k] * Xout[(int64_t)k * L + c];
-      Xout[(int64_t)i * L + c] = s / A[(int64_t)i * L + i];
+      double s = 0.0;
+      for (int k = sub; k < i; k += gs) s += A[(int64_t)i * L + k] * Xout[(int64_t)k * L + c];
+      for (int o = gs / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, gs);
+      if (live && sub == 0) Xout[(int64_t)i * L + c] = ((i == c ? 1.0 : 0.0) - s) / A[(int64_t)i * L + i];
+      __syncwarp();
     }
     for (int i = L - 1; i >= 0; --i) {  // backward: G^T x = y
-      double s = Xout[(int64_t)i * L + c];
-      for (int k = i + 1; k < L; ++k) s -= A[(int64_t)k * L + i] * Xout[(int64_t)k * L + c];
-      Xout[(int64_t)i * L + c] = s / A[(int64_t)i * L + i];
+      double s = 0.0;
+      for (int k = i + 1 + sub; k < L; k += gs) s += A[(int64_t)k * L + i] * Xout[(int64_t)k * L + c];
+      for (int o = gs / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, gs);
+      if (live && sub == 0) Xout[(int64_t)i * L + c] = (Xout[(int64_t)i * L + c] - s) / A[(int64_t)i * L + i];
+      __syncwarp();
     }
   }
   __syncthreads();
@@ -219,6 +263,7 @@ int read_dev_err(int* derr, cudaStream_t s) {
 
 int schur_matrix(zi_system* S, double* Sm, cudaStream_t s) {
   const int L = S->n_el;
+  if (L > 256) return set_error(ZI_ERR_ARG, "more than 256 electrodes");
   k_schur<<<L, 256, 0, s>>>(L, S->n_patch_nodes, S->patch_nodes, S->B, S->T, S->C, Sm);
   ZI_LAUNCH_CHECK();
   return ZI_OK;
