@@ -113,10 +113,10 @@ __global__ void __launch_bounds__(256) k_schur(int L, int64_t np_, const int32_t
   if (threadIdx.x < L) S[(int64_t)k * L + threadIdx.x] = (k == (int)threadIdx.x ? C[k] : 0.0) - s;
 }
 
-// Single block: Cholesky factor of the SPD L x L matrix A (in place, lower),
-// then Xout = R A^-1 (R = I - 11^T/L) when avg_ref, else A^-1.
-__global__ void __launch_bounds__(1024) k_chol_inverse(int L, double* __restrict__ A, double* __restrict__ Xout,
-                                                       int avg_ref, int* __restrict__ err) {
+// Single block: Cholesky factor A = G G^T of the SPD L x L matrix, in place
+// (G in the lower triangle, G^T mirrored into the upper one); a non-positive
+// pivot sets DEV_ERR_NOT_SPD.  k_chol_solve then forms (R) A^-1.
+__global__ void __launch_bounds__(1024) k_chol(int L, double* __restrict__ A, int* __restrict__ err) {
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
@@ -129,7 +129,11 @@ __global__ void __launch_bounds__(1024) k_chol_inverse(int L, double* __restrict
     __syncthreads();
     if (bad) break;
     double sd = sqrt(d);
-    for (int i = j + 1 + threadIdx.x; i < L; i += blockDim.x) A[(int64_t)i * L + j] /= sd;
+    for (int i = j + 1 + threadIdx.x; i < L; i += blockDim.x) {
+      const double g = A[(int64_t)i * L + j] / sd;
+      A[(int64_t)i * L + j] = g;
+      A[(int64_t)j * L + i] = g;  // G^T in the upper triangle, for row-wise back substitution
+    }
     __syncthreads();
     if (threadIdx.x == 0) A[(int64_t)j * L + j] = sd;
     // trailing update of the lower triangle: A[i][k] -= A[i][j] A[k][j], j < k <= i
@@ -146,45 +150,39 @@ __global__ void __launch_bounds__(1024) k_chol_inverse(int L, double* __restrict
     }
     __syncthreads();
   }
-  if (bad) {
-    if (threadIdx.x == 0) atomicOr(err, DEV_ERR_NOT_SPD);
-    return;
+  if (bad && threadIdx.x == 0) atomicOr(err, DEV_ERR_NOT_SPD);
+}
+
+// Column c of Xout = A^-1 (A = G G^T from k_chol), one warp per column:
+// forward G y = e_c and backward G^T x = y, each step a warp-wide dot (lane l
+// takes k = l mod 32) over y / x held in shared memory.  avg_ref: then
+// x -= mean(x) (the average-reference rows of R S^-1).
+__global__ void __launch_bounds__(32) k_chol_solve(int L, const double* __restrict__ A, double* __restrict__ Xout,
+                                                   int avg_ref, const int* __restrict__ err) {
+  if (*(volatile const int*)err) return;
+  __shared__ double y[256];
+  const int c = blockIdx.x, lane = threadIdx.x;
+  for (int i = 0; i < L; ++i) {
+    double s = 0.0;
+    for (int k = lane; k < i; k += 32) s += A[(int64_t)i * L + k] * y[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[i] = ((i == c ? 1.0 : 0.0) - s) / A[(int64_t)i * L + i];
+    __syncwarp();
   }
-  // Xout = A^-1: column c solves (G G^T) x = e_c.  A group of gs lanes of one
-  // warp (gs = the largest power of two <= min(32, blockDim / L)) shares a
-  // column: lane `sub` of the group sums the terms k = sub (mod gs) of every
-  // substitution step, the group adds them with shuffles, and lane 0 writes
-  // the new entry, which __syncwarp makes visible to the group.
-  int gs = 1;
-  while (gs * 2 <= 32 && gs * 2 * L <= (int)blockDim.x) gs *= 2;
-  const int sub = threadIdx.x % gs, ngroups = blockDim.x / gs;
-  for (int c0 = threadIdx.x / gs; c0 - (int)(threadIdx.x / gs) < L; c0 += ngroups) {
-    const bool live = c0 < L;   // idle groups run the loop too (shuffle partners), writing nothing
-    const int c = live ? c0 : L - 1;
-    for (int i = 0; i < L; ++i) {  // forward: G y = e_c, y stored in Xout[:, c]
-      double s = 0.0;
-      for (int k = sub; k < i; k += gs) s += A[(int64_t)i * L + k] * Xout[(int64_t)k * L + c];
-      for (int o = gs / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, gs);
-      if (live && sub == 0) Xout[(int64_t)i * L + c] = ((i == c ? 1.0 : 0.0) - s) / A[(int64_t)i * L + i];
-      __syncwarp();
-    }
-    for (int i = L - 1; i >= 0; --i) {  // backward: G^T x = y
-      double s = 0.0;
-      for (int k = i + 1 + sub; k < L; k += gs) s += A[(int64_t)k * L + i] * Xout[(int64_t)k * L + c];
-      for (int o = gs / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, gs);
-      if (live && sub == 0) Xout[(int64_t)i * L + c] = (Xout[(int64_t)i * L + c] - s) / A[(int64_t)i * L + i];
-      __syncwarp();
-    }
+  for (int i = L - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int k = i + 1 + lane; k < L; k += 32) s += A[(int64_t)i * L + k] * y[k];  // upper triangle = G^T
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[i] = (y[i] - s) / A[(int64_t)i * L + i];
+    __syncwarp();
   }
-  __syncthreads();
+  double mean = 0.0;
   if (avg_ref) {
-    for (int c = threadIdx.x; c < L; c += blockDim.x) {
-      double mean = 0.0;
-      for (int i = 0; i < L; ++i) mean += Xout[(int64_t)i * L + c];
-      mean /= L;
-      for (int i = 0; i < L; ++i) Xout[(int64_t)i * L + c] -= mean;
-    }
+    for (int i = lane; i < L; i += 32) mean += y[i];
+    for (int o = 16; o > 0; o >>= 1) mean += __shfl_xor_sync(0xffffffffu, mean, o);
+    mean /= L;
   }
+  for (int i = lane; i < L; i += 32) Xout[(int64_t)i * L + c] = y[i] - mean;
 }
 
 // Out[r][j] = sum_k A[r][k] * Ht[j][k]   (Out: Lr x N, A: Lr x K, Ht: N x K),
@@ -274,7 +272,10 @@ int schur_inverse(zi_system* S, double* Sm, double* Xout, int avg_ref, cudaStrea
   DevTmp<int> err;
   ZI_CHECK(err.alloc(1, s));
   ZI_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-  k_chol_inverse<<<1, 1024, 0, s>>>(S->n_el, Sm, Xout, avg_ref, err.p);
+  if (S->n_el > 256) return set_error(ZI_ERR_ARG, "more than 256 electrodes");
+  k_chol<<<1, 1024, 0, s>>>(S->n_el, Sm, err.p);
+  ZI_LAUNCH_CHECK();
+  k_chol_solve<<<S->n_el, 32, 0, s>>>(S->n_el, Sm, Xout, avg_ref, err.p);
   ZI_LAUNCH_CHECK();
   return read_dev_err(err.p, s);
 }
@@ -408,7 +409,9 @@ extern "C" int zi_leadfield_noalloc(zi_system* S, const int32_t* dip_tet, int64_
   const int64_t N = 3 * P;
   if (cem) {
     ZI_CHECK(schur_matrix(S, Sm, s));
-    k_chol_inverse<<<1, 1024, 0, s>>>(L, Sm, Wm, 1, err);
+    k_chol<<<1, 1024, 0, s>>>(L, Sm, err);
+    ZI_LAUNCH_CHECK();
+    k_chol_solve<<<L, 32, 0, s>>>(L, Sm, Wm, 1, err);
     ZI_LAUNCH_CHECK();
     ZI_CHECK(noalloc_read_err(err, s));
     dim3 grid((unsigned)((N + GT - 1) / GT), (unsigned)((L + GT - 1) / GT));

@@ -948,39 +948,40 @@ __global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ w, co
   extern __shared__ double sred[];
   const int nq = ld / 4;
   const int c = threadIdx.x % nq, g = threadIdx.x / nq, rpb = blockDim.x / nq;
-  double rr[4] = {0.0, 0.0, 0.0, 0.0};
+  // FP32 arithmetic (the inner solve's precision): FP64 operations run at a
+  // small fraction of the FP32 rate on this GPU and would bound the pass
+  float rr[4] = {0.f, 0.f, 0.f, 0.f};
   if (g < rpb) {
-    double gi[4];
-    float ratio[4];
+    float gi[4], ratio[4];
     bool kp[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int col = 4 * c + k;
-      gi[k] = gamma[col] > 0.0 ? 1.0 / gamma[col] : 0.0;
+      gi[k] = gamma[col] > 0.0 ? (float)(1.0 / gamma[col]) : 0.f;
       kp[k] = keep_p && gamma[col] > 0.0 && gamma_prev[col] > 0.0;
-      ratio[k] = kp[k] ? (float)(gamma_prev[col] * gi[k]) : 0.f;
+      ratio[k] = kp[k] ? (float)(gamma_prev[col] / gamma[col]) : 0.f;
     }
     for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
       const int64_t e = i * ld + 4 * c;
       const double2 ra = *reinterpret_cast<const double2*>(R64 + e);
       const double2 rb = *reinterpret_cast<const double2*>(R64 + e + 2);
-      const double r64[4] = {ra.x, ra.y, rb.x, rb.y};
-      const double wi = w[i];
+      const float r64[4] = {(float)ra.x, (float)ra.y, (float)rb.x, (float)rb.y};
+      const float wi = (float)w[i];
       float4 pold = keep_p ? *reinterpret_cast<const float4*>(p32 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
       const float po[4] = {pold.x, pold.y, pold.z, pold.w};
       float r[4], pn[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        r[k] = (float)(r64[k] * gi[k]);
-        pn[k] = kp[k] ? po[k] * ratio[k] : (float)wi * r[k];
-        rr[k] += wi * (double)r[k] * (double)r[k];
+        r[k] = r64[k] * gi[k];
+        pn[k] = kp[k] ? po[k] * ratio[k] : wi * r[k];
+        rr[k] += wi * r[k] * r[k];
       }
       *reinterpret_cast<float4*>(r32 + e) = make_float4(r[0], r[1], r[2], r[3]);
       *reinterpret_cast<float4*>(p32 + e) = make_float4(pn[0], pn[1], pn[2], pn[3]);
       *reinterpret_cast<float4*>(x32 + e) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) sred[g * ld + 4 * c + k] = rr[k];
+    for (int k = 0; k < 4; ++k) sred[g * ld + 4 * c + k] = (double)rr[k];
   }
   __syncthreads();
   for (int col = threadIdx.x; col < ld; col += blockDim.x) {
