@@ -62,7 +62,11 @@ enum { ZI_ELECTRODE_POINT = 0, ZI_ELECTRODE_CEM = 1 };
  * diagonal preconditioner 1/sum_j |a_ij|. */
 enum { ZI_PRECOND_JACOBI = 0, ZI_PRECOND_LDP = 1 };
 /* Solver precision: FP64 throughout, or FP32 inner PCG inside FP64 iterative
- * refinement (FP64 residual b - A x and solution update). */
+ * refinement (FP64 residual b - A x and solution update).  The FP32 solve
+ * works on the unscaled matrix in difference form, c_i p_i + sum_j a_ij
+ * (p_j - p_i) with c_i the row sum, which avoids the cancellation of the plain
+ * stencil on smooth vectors.  Both precisions omit couplings at assembly
+ * rounding level (|a_ij| <= 2^-40 sqrt(a_ii a_jj); FP32: <= 2^-24). */
 enum { ZI_FP64 = 0, ZI_MIXED = 1 };
 /* EIT output modes. */
 enum { ZI_EIT_FULL = 0, ZI_EIT_VJP = 1 };
@@ -278,7 +282,7 @@ int zi_leadfield_noalloc(zi_system* sys, const int32_t* dip_tet, int64_t P, doub
 
 /* Times the solver's sparse matrix product (the multi-RHS SpMM fused with the
  * column dots, the kernel of each CG iteration) on the system's current
- * scaled matrix and work vectors: `reps` launches on the library's stream,
+ * solver matrix and work vectors: `reps` launches on the library's stream,
  * each bracketed by CUDA events, with a write of a 256 MB buffer between
  * launches so the next one starts with a cold L2.  precision: ZI_FP64 or
  * ZI_MIXED (FP32 product).  Requires a prior zi_transfer with the same
