@@ -311,9 +311,12 @@ constexpr int ELL_K = 8;
 // depend on are already on chip (loading them from HBM per row put one HBM
 // round trip in front of every row's gathers).
 constexpr int ELL_NBUF = 2;
+// Row groups per chunk: 8 (a sweep over 4 to 32 on the 2 mm and 1 mm heads put
+// the optimum there), fewer for narrow rows so that a chunk stays <= 256 rows.
+constexpr int ELL_MAXSLOTS = 8;
 __host__ __device__ inline int ell_chunk_slots(int rpb) {
-  const int sl = 128 / rpb;
-  return sl < 1 ? 1 : (sl > 4 ? 4 : sl);
+  const int sl = (32 * ELL_MAXSLOTS) / rpb;
+  return sl < 1 ? 1 : (sl > ELL_MAXSLOTS ? ELL_MAXSLOTS : sl);
 }
 __host__ __device__ inline size_t ell_sred_bytes(int tpr, int ld) {
   return ((size_t)(BLOCK_THREADS / tpr) * ld * sizeof(double) + 127) / 128 * 128;
@@ -439,12 +442,25 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
           for (int u = 1; u < ELL_K; ++u) vfma_diff(acc[v], a[u], x[u][v], x[0][v]);
         }
         if (tail) {
+          // the tail in batches of four: indices and values first, then the gathers
           const int t0 = __ldg(tail_ptr + i), t1 = __ldg(tail_ptr + i + 1);
-          for (int t = t0; t < t1; ++t) {
-            const int jj = __ldg(tail_ci + t);
-            const float aa = __ldg(tail_va + t);
+          for (int t = t0; t < t1; t += 4) {
+            int jt[4];
+            float at[4];
 #pragma unroll
-            for (int v = 0; v < CPTV; ++v) vfma_diff(acc[v], aa, ldg_v(Pv + (jj * nv + v * tpr)), x[0][v]);
+            for (int u = 0; u < 4; ++u) {
+              const bool in = t + u < t1;
+              jt[u] = in ? __ldg(tail_ci + t + u) : -1;
+              at[u] = in ? __ldg(tail_va + t + u) : 0.f;
+            }
+#pragma unroll
+            for (int v = 0; v < CPTV; ++v) {
+              V xt[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) xt[u] = jt[u] >= 0 ? ldg_v(Pv + (jt[u] * nv + v * tpr)) : x[0][v];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) vfma_diff(acc[v], at[u], xt[u], x[0][v]);
+            }
           }
         }
 #pragma unroll

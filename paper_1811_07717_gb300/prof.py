@@ -28,13 +28,15 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--iters", type=int, default=1, help="CG iterations before the standalone launches")
+    ap.add_argument("--aniso", action="store_true", help="transversely anisotropic skull (radial 0.00132, "
+                    "tangential 0.0132 S/m)")
     a = ap.parse_args()
     import torch
 
     from paper_1811_07717_gb300 import workloads as W
     from paper_1811_07717_gb300 import zi
 
-    spec = W.three_shell(a.h, a.electrodes, 10, seed=2)
+    spec = W.three_shell(a.h, a.electrodes, 10, seed=2, skull_aniso=(0.00132, 0.0132) if a.aniso else None)
     mesh = zi.mesh_from_grid(spec.h, spec.radii)
     s6 = W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(),
                         mesh["labels"].cpu().numpy())
