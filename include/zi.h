@@ -70,6 +70,8 @@ enum { ZI_PRECOND_JACOBI = 0, ZI_PRECOND_LDP = 1 };
 enum { ZI_FP64 = 0, ZI_MIXED = 1 };
 /* EIT output modes. */
 enum { ZI_EIT_FULL = 0, ZI_EIT_VJP = 1 };
+/* IAS hypermodels (App. B): gamma (G) and inverse gamma (IG). */
+enum { ZI_HYPER_G = 0, ZI_HYPER_IG = 1 };
 
 typedef struct zi_system zi_system;
 
@@ -275,6 +277,29 @@ int zi_eit_jacobian(zi_system* sys, const double* I, int np, int mode,
  * Synchronises the stream. */
 int zi_leadfield_noalloc(zi_system* sys, const int32_t* dip_tet, int64_t P, double* L,
                          cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* IAS MAP inversion (App. B)                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Iterative alternating sequential MAP estimates for T data vectors, each
+ * inverted on its own: theta = theta0 for every source, then `iters` rounds of
+ *   x     = D L^T (L D L^T + nu^2 I)^-1 y,   D = diag(theta)   (App. B, Eq. ias_matrix;
+ *           the paper's D^{1/2} L_k^T with L_k = L D^{1/2}, theta > 0)
+ *   theta = theta0/2 (eta + sqrt(eta^2 + 2 x^2/theta0)), eta = beta - 3/2    (ZI_HYPER_G)
+ *         or (theta0 + x^2/2) / (beta + 3/2)                                (ZI_HYPER_IG)
+ * elementwise.  L D L^T is an FP64 product over the sources split across the
+ * GPU; the Le x Le systems are solved by Cholesky.
+ *   L:     device in, Le x n f64 row-major (a lead field, e.g. from zi_leadfield); 1 <= Le <= 256.
+ *   Y:     device in, T x Le f64 (data vector t in row t).
+ *   X:     device out, T x n f64 (the estimate of data vector t in row t).
+ *   Theta: device out, T x n f64 (the final hyperparameters).
+ * nu > 0 (noise standard deviation), theta0 > 0; IG needs beta > -3/2.  With
+ * G and beta <= 3/2 a source whose estimate reaches zero stays at zero.
+ * ZI_ERR_ARG for bad sizes or parameters.  Scratch comes from the library's
+ * pool.  Synchronises. */
+int zi_ias_map(const double* L, int32_t Le, int64_t n, const double* Y, int32_t T, double nu, double theta0,
+               double beta, int32_t hypermodel, int32_t iters, double* X, double* Theta, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Diagnostics (no counterpart in the paper: measurement support)             */

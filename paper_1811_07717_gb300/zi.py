@@ -22,13 +22,14 @@ ELECTRODE_POINT, ELECTRODE_CEM = 0, 1
 PRECOND_JACOBI, PRECOND_LDP = 0, 1
 FP64, MIXED = 0, 1
 EIT_FULL, EIT_VJP = 0, 1
+HYPER_G, HYPER_IG = 0, 1
 
 # Every symbol include/zi.h declares.
 EXPORTS = ("zi_version", "zi_last_error", "zi_status_string", "zi_mesh_from_grid",
            "zi_locate_dipoles_grid", "zi_assemble", "zi_system_set_conductivity",
            "zi_system_get_info", "zi_system_get_matrix", "zi_system_destroy",
            "zi_solver_opts_default", "zi_transfer", "zi_transfer_batched", "zi_leadfield",
-           "zi_eit_jacobian", "zi_leadfield_noalloc", "zi_time_spmm", "zi_kernel_launches")
+           "zi_eit_jacobian", "zi_leadfield_noalloc", "zi_ias_map", "zi_time_spmm", "zi_kernel_launches")
 
 
 class ZiError(RuntimeError):
@@ -89,6 +90,7 @@ def load_library(path: str = LIB_PATH):
         "zi_leadfield": ([P, P, I64, ctypes.POINTER(_Opts), P, P], ctypes.c_int),
         "zi_eit_jacobian": ([P, P, ctypes.c_int, ctypes.c_int, P, P, P, ctypes.POINTER(_Opts), P], ctypes.c_int),
         "zi_leadfield_noalloc": ([P, P, I64, P, P], ctypes.c_int),
+        "zi_ias_map": ([P, I32, I64, P, I32, D, D, D, I32, I32, P, P, P], ctypes.c_int),
         "zi_time_spmm": ([P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(D), ctypes.POINTER(D), P], ctypes.c_int),
         "zi_kernel_launches": ([], ctypes.c_int64),
     }
@@ -353,3 +355,23 @@ def transfer_batched(systems, opts: SolverOpts | None = None, want_T: bool = Fal
     o = opts.c()
     _check(lib.zi_transfer_batched(hs, nb, ctypes.byref(o), Tp, itp, _stream()))
     return Ts, [np.array(it[:], dtype=np.int32) for it in its]
+
+
+def ias_map(L, Y, nu: float, theta0: float, beta: float, hypermodel: int = HYPER_G, iters: int = 20):
+    """IAS MAP inversion (App. B, zi_ias_map) of the data vectors Y (T x Le
+    CUDA tensor, or Le for one) with the lead field L (Le x n CUDA tensor);
+    returns X and Theta (T x n, or n for one data vector)."""
+    torch = _torch()
+    lib = load_library()
+    L = L.contiguous().to(torch.float64)
+    one = Y.dim() == 1
+    Y = (Y[None, :] if one else Y).contiguous().to(torch.float64)
+    Le, n = L.shape
+    T = Y.shape[0]
+    if Y.shape[1] != Le:
+        raise ValueError("Y must have Le = %d columns" % Le)
+    X = torch.empty((T, n), dtype=torch.float64, device=L.device)
+    Th = torch.empty((T, n), dtype=torch.float64, device=L.device)
+    _check(lib.zi_ias_map(_ptr(L), Le, n, _ptr(Y), T, float(nu), float(theta0), float(beta), int(hypermodel),
+                          int(iters), _ptr(X), _ptr(Th), _stream()))
+    return (X[0], Th[0]) if one else (X, Th)
