@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison build")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="shell2mm", choices=["shell2mm", "aniso1mm", "batch"],
+    ap.add_argument("--workload", default="shell2mm", choices=["shell2mm", "aniso1mm", "batch", "ias"],
                     help="shell2mm: the headline workload; aniso1mm: 1 mm anisotropic-skull head, 256 "
                          "electrodes, 100k dipoles; batch: 24 heads, batched vs per-head solves")
     return ap.parse_args()
@@ -288,6 +288,90 @@ def batch_workload(args):
 
 
 # ---------------------------------------------------------------------------
+# IAS MAP inversion (App. B) on the 2 mm lead field
+# ---------------------------------------------------------------------------
+
+def ias_oracle_once(L, Y, nu, theta0, beta, rounds) -> float:
+    """The oracle's IAS on a bounded sample of the data vectors, in a fresh
+    single-threaded process (seconds)."""
+    import tempfile as _tf
+    with _tf.TemporaryDirectory() as td:
+        np.save(os.path.join(td, "L.npy"), L)
+        np.save(os.path.join(td, "Y.npy"), Y)
+        code = ("import sys,time,numpy as np; sys.path.insert(0, %r)\n"
+                "from oracle import ias as I\n"
+                "L = np.load(%r); Y = np.load(%r)\n"
+                "t = time.perf_counter(); I.ias_map(L, Y, %r, %r, %r, I.HYPER_G, %d); print(time.perf_counter() - t)\n"
+                % (ROOT, os.path.join(td, "L.npy"), os.path.join(td, "Y.npy"), nu, theta0, beta, rounds))
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+        if r.returncode != 0:
+            raise RuntimeError("IAS oracle sample failed: " + r.stderr[-500:])
+        return float(r.stdout.strip().splitlines()[-1])
+
+
+def ias_workload(args):
+    """IAS rounds for 16 data vectors with the 2 mm lead field (128 x 60000):
+    time per round and the FP64 rate of the Gram product that bounds it."""
+    import torch
+    from paper_1811_07717_gb300 import workloads as W
+    from paper_1811_07717_gb300 import _build, zi
+    _build.build()
+    spec = W.config_three_shell_2mm()
+    mesh = zi.mesh_from_grid(spec.h, spec.radii)
+    s6 = W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(),
+                        mesh["labels"].cpu().numpy())
+    centres, z = W.electrode_inputs(spec)
+    pos, _ = W.dipole_inputs(spec)
+    system = zi.System(mesh["nodes"], mesh["tets"], s6, mesh["bfaces"], centres, model="cem", z=z,
+                       radius=spec.electrode_radius)
+    L = system.leadfield(zi.locate_dipoles_grid(spec.h, spec.radii, pos), zi.SolverOpts(tol=1e-10,
+                                                                                        precision=zi.MIXED))
+    system.close()
+    Le, n = L.shape
+    T, rounds = 16, 20
+    rng = np.random.default_rng(7)
+    Xt = np.zeros((n, T))
+    Xt[rng.choice(n, 5, replace=False), :] = rng.standard_normal((5, T)) * 1e-8
+    Yh = L.cpu().numpy() @ Xt
+    nu = 0.05 * float(np.abs(Yh).max())
+    Yh = Yh + nu * rng.standard_normal(Yh.shape)
+    Y = torch.from_numpy(Yh.T.copy()).cuda()
+    theta0, beta = 1e-16, 1.6
+    for _ in range(max(1, args.warmup)):
+        zi.ias_map(L, Y, nu, theta0, beta, zi.HYPER_G, rounds)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with Clocks(torch.cuda.current_device()) as clk:
+        t0.record()
+        for _ in range(args.steps):
+            zi.ias_map(L, Y, nu, theta0, beta, zi.HYPER_G, rounds)
+        t1.record()
+        torch.cuda.synchronize()
+    sec = t0.elapsed_time(t1) / 1e3 / args.steps
+    tiles = ((Le + 31) // 32) * ((Le + 31) // 32 + 1) // 2
+    flops = rounds * T * (2.0 * tiles * 32 * 32 * n + 2.0 * Le * n)   # Gram tiles computed + L^T z
+    peak_tf = 1.25  # nominal FP64 rate of the part (no measured FP64 figure is available)
+    line = {"metric": "IAS MAP inversion s (20 rounds, 16 data vectors, 2 mm lead field 128 x 60000)",
+            "value": sec, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "IAS (App. B), gamma hypermodel, theta0 1e-16, beta 1.6, nu 5% of max |y|",
+                       "Le": Le, "n": n, "data_vectors": T, "rounds": rounds},
+            "roofline": {"bound": "alu", "kernel": "k_ias_gram (FP64 split-K Gram product)",
+                         "achieved": flops / sec / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": flops / sec / 1e12 / peak_tf, "peak_note": "nominal FP64", "traffic": None},
+            "clocks": clk.summary()}
+    if not args.no_cpu:
+        try:
+            c = ias_oracle_once(L.cpu().numpy(), Yh[:, :2], nu, theta0, beta, rounds)
+            line["cpu_baseline"] = {"value": c * T / 2, "unit": "s", "cores": 1, "kind": "oracle",
+                                    "sample": "2 of the 16 data vectors (numpy, 1 thread), scaled to 16"}
+        except Exception as ex:
+            line["cpu_baseline"] = {"value": None, "sample": "failed: %s" % ex}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -311,6 +395,8 @@ def main():
 
     if args.workload == "batch":
         return batch_workload(args)
+    if args.workload == "ias":
+        return ias_workload(args)
     spec = W.config_three_shell_2mm() if args.workload == "shell2mm" else W.config_three_shell_1mm_aniso()
     workload = WORKLOAD if args.workload == "shell2mm" else (
         "three-shell sphere 80/86/92 mm, h=1 mm Kuhn grid (3342701 nodes, 19573872 tets), transversely "
