@@ -321,10 +321,11 @@ __host__ __device__ inline int ell_chunk_slots(int rpb) {
 __host__ __device__ inline size_t ell_sred_bytes(int tpr, int ld) {
   return ((size_t)(BLOCK_THREADS / tpr) * ld * sizeof(double) + 127) / 128 * 128;
 }
-__host__ __device__ inline size_t ell_smem_bytes(int tpr, int ld) {
+__host__ __device__ inline size_t ell_smem_bytes(int tpr, int ld, bool ovf) {
   const int rpb = BLOCK_THREADS / tpr;
   const size_t C = (size_t)ell_chunk_slots(rpb) * rpb;
-  return ell_sred_bytes(tpr, ld) + (size_t)ELL_NBUF * 2 * C * 32;  // ci (int4 x 2) + va (float4 x 2) per row
+  // ci (int4 x 2) + va (float4 x 2) per row, twice with the overflow slots
+  return ell_sred_bytes(tpr, ld) + (size_t)ELL_NBUF * (ovf ? 4 : 2) * C * 32;
 }
 
 constexpr long long MBAR_SPIN_LIMIT = 1 << 22;  // a few ms of polling before a copy is given up on
@@ -363,9 +364,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 // + C - 1 (G blocks); row group g takes rows g, g + rpb, ... of a chunk.  On a
 // copy that never completes the kernel sets DEV_ERR_TIMEOUT in *err, waits
 // (bounded) for its other copies and still joins the cluster reduction.
-template <int CPTV>
+template <int CPTV, bool OVF>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1 ? 4 : 2)
     k_spmm_ell(int64_t n, int tpr, const int4* __restrict__ ci, const float4* __restrict__ va,
+               const int4* __restrict__ oci, const float4* __restrict__ ova,
                const int32_t* __restrict__ tail_ptr, const int32_t* __restrict__ tail_ci,
                const float* __restrict__ tail_va, const float* __restrict__ P, float* __restrict__ Q, int ld,
                double* __restrict__ partial, int* __restrict__ cnt, int freeze, int* __restrict__ err) {
@@ -385,6 +387,9 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
   const int slots = ell_chunk_slots(rpb), C = slots * rpb;
   int4* sci = reinterpret_cast<int4*>(smem_raw + ell_sred_bytes(tpr, ld));  // [ELL_NBUF][2 C]
   float4* sva = reinterpret_cast<float4*>(sci + ELL_NBUF * 2 * C);           // [ELL_NBUF][2 C]
+  int4* soc = reinterpret_cast<int4*>(sva + ELL_NBUF * 2 * C);               // overflow slots, if any
+  float4* sov = reinterpret_cast<float4*>(soc + ELL_NBUF * 2 * C);
+  constexpr bool ovf = OVF;  // overflow slots staged with the row's own (oci, ova non-null)
   float acc_pq[CPTV][W];
 #pragma unroll
   for (int v = 0; v < CPTV; ++v)
@@ -400,9 +405,13 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
   __syncthreads();
   auto issue = [&](int b, int64_t cb) {  // one thread: copy chunk cb's slots into buffer b
     const unsigned bytes = (unsigned)min((int64_t)C, n - cb) * 32u;
-    mbar_expect_tx(&bar[b], 2u * bytes);
+    mbar_expect_tx(&bar[b], (ovf ? 4u : 2u) * bytes);
     bulk_g2s(sci + b * 2 * C, ci + 2 * cb, bytes, &bar[b]);
     bulk_g2s(sva + b * 2 * C, va + 2 * cb, bytes, &bar[b]);
+    if (ovf) {
+      bulk_g2s(soc + b * 2 * C, oci + 2 * cb, bytes, &bar[b]);
+      bulk_g2s(sov + b * 2 * C, ova + 2 * cb, bytes, &bar[b]);
+    }
   };
   if (threadIdx.x == 0)
     for (int b = 0; b < ELL_NBUF; ++b)
@@ -442,8 +451,25 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
           for (int u = 1; u < ELL_K; ++u) vfma_diff(acc[v], a[u], x[u][v], x[0][v]);
         }
         if (tail) {
+          int t0 = __ldg(tail_ptr + i);
+          const int t1 = __ldg(tail_ptr + i + 1);
+          if (ovf) {
+            // the first eight tail entries, staged like the row's own slots
+            const int4 o0 = soc[b * 2 * C + 2 * lr], o1 = soc[b * 2 * C + 2 * lr + 1];
+            const float4 w0 = sov[b * 2 * C + 2 * lr], w1 = sov[b * 2 * C + 2 * lr + 1];
+            const int jo[ELL_K] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+            const float ao[ELL_K] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int v = 0; v < CPTV; ++v) {
+              V xo[ELL_K];
+#pragma unroll
+              for (int u = 0; u < ELL_K; ++u) xo[u] = jo[u] >= 0 ? ldg_v(Pv + (jo[u] * nv + v * tpr)) : x[0][v];
+#pragma unroll
+              for (int u = 0; u < ELL_K; ++u) vfma_diff(acc[v], ao[u], xo[u], x[0][v]);
+            }
+            t0 = min(t0 + ELL_K, t1);
+          }
           // the tail in batches of four: indices and values first, then the gathers
-          const int t0 = __ldg(tail_ptr + i), t1 = __ldg(tail_ptr + i + 1);
           for (int t = t0; t < t1; t += 4) {
             int jt[4];
             float at[4];
@@ -800,10 +826,30 @@ __global__ void k_fill32(int64_t n, const int32_t* __restrict__ rowptr, const in
 // ELL copy of the compacted FP32 matrix: row i's first ELL_K entries in slots
 // [i*ELL_K, (i+1)*ELL_K), the diagonal first, then the others in CSR order,
 // padding -1 / 0; entries past ELL_K go to the tail at tail_ptr[i].
-__global__ void k_tail_count(int64_t n, const int32_t* __restrict__ rowptr32, int32_t* __restrict__ tcnt) {
+__global__ void k_tail_count(int64_t n, const int32_t* __restrict__ rowptr32, int32_t* __restrict__ tcnt,
+                             int* __restrict__ nrows) {
+  int mine = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int c = rowptr32[i + 1] - rowptr32[i];
     tcnt[i] = c > ELL_K ? c - ELL_K : 0;
+    mine += c > ELL_K ? 1 : 0;
+  }
+  if (mine) atomicAdd(nrows, mine);
+}
+
+// Overflow slots of the rows with a tail: their first ELL_K tail entries in
+// the ELL layout (padding -1 / 0), so that the SpMM stages them with the
+// row's own slots; built when many rows have a tail (anisotropic elements
+// couple all 14 Kuhn neighbours).
+__global__ void k_fill_ovf(int64_t n, const int32_t* __restrict__ tail_ptr, const int32_t* __restrict__ tail_ci,
+                           const float* __restrict__ tail_va, int32_t* __restrict__ oci, float* __restrict__ ova) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int t0 = tail_ptr[i], t1 = tail_ptr[i + 1];
+    for (int u = 0; u < ELL_K; ++u) {
+      const bool in = t0 + u < t1;
+      oci[i * ELL_K + u] = in ? tail_ci[t0 + u] : -1;
+      ova[i * ELL_K + u] = in ? tail_va[t0 + u] : 0.f;
+    }
   }
 }
 
@@ -1054,6 +1100,8 @@ struct SolverScratch {
   int32_t* ell_ci = nullptr;    // n x ELL_K
   float* ell_va = nullptr;      // n x ELL_K
   int32_t* tail_ptr = nullptr;  // n + 1 (null when no row exceeds ELL_K)
+  int32_t* ovf_ci = nullptr;    // n x ELL_K overflow slots (null unless many rows have a tail)
+  float* ovf_va = nullptr;
   int64_t ntail = 0;
   int32_t* tail_ci = nullptr;
   float* tail_va = nullptr;
@@ -1088,7 +1136,7 @@ void solver_scratch_free(zi_system* S) {
   SolverScratch* w = S ? S->solver : nullptr;
   if (!w) return;
   cudaStream_t s = 0;
-  void* ptrs[] = {w->s, w->dtrue, w->w32, w->v64, w->rowptrc, w->colindc, w->valsc, w->v32, w->rowptr32, w->colind32, w->ell_ci, w->ell_va, w->tail_ptr, w->tail_ci, w->tail_va, w->X, w->R, w->P, w->Q, w->x32, w->r32, w->p32, w->q32,
+  void* ptrs[] = {w->s, w->dtrue, w->w32, w->v64, w->rowptrc, w->colindc, w->valsc, w->v32, w->rowptr32, w->colind32, w->ell_ci, w->ell_va, w->tail_ptr, w->tail_ci, w->tail_va, w->ovf_ci, w->ovf_va, w->X, w->R, w->P, w->Q, w->x32, w->r32, w->p32, w->q32,
                   w->part0, w->part1, w->part2, w->rho, w->alpha, w->beta, w->stop2, w->bb, w->vec,
                   w->conv, w->iters, w->cnt, w->gamma, w->gamma_prev, w->flag, w->nact, w->bar, w->gpart};
   for (void* p : ptrs) dfree(p, s);
@@ -1145,16 +1193,29 @@ int launch_spmm(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int6
 }
 
 int launch_spmm_ell(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, const int32_t* ci,
-                    const float* va, const int32_t* tptr, const int32_t* tci, const float* tva, const float* P,
-                    float* Q, int ld, double* part, int* err, int* cnt = nullptr, int freeze = 1) {
+                    const float* va, const int32_t* oci, const float* ova, const int32_t* tptr, const int32_t* tci,
+                    const float* tva, const float* P, float* Q, int ld, double* part, int* err, int* cnt = nullptr,
+                    int freeze = 1) {
   const int4* c4 = reinterpret_cast<const int4*>(ci);
   const float4* v4 = reinterpret_cast<const float4*>(va);
+  const int4* o4 = reinterpret_cast<const int4*>(oci);
+  const float4* w4 = reinterpret_cast<const float4*>(ova);
+#define ZI_ELL_CASE(CV)                                                                                     \
+  case CV:                                                                                                   \
+    if (o4)                                                                                                  \
+      k_spmm_ell<CV, true><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, o4, w4, tptr, tci, tva, P, Q, ld, part, \
+                                                      cnt, freeze, err);                                     \
+    else                                                                                                     \
+      k_spmm_ell<CV, false><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, o4, w4, tptr, tci, tva, P, Q, ld,      \
+                                                       part, cnt, freeze, err);                              \
+    break;
   switch (cptv) {
-    case 1: k_spmm_ell<1><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part, cnt, freeze, err); break;
-    case 2: k_spmm_ell<2><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part, cnt, freeze, err); break;
-    case 4: k_spmm_ell<4><<<grid, BLOCK, smem, st>>>(n, tpr, c4, v4, tptr, tci, tva, P, Q, ld, part, cnt, freeze, err); break;
+    ZI_ELL_CASE(1)
+    ZI_ELL_CASE(2)
+    ZI_ELL_CASE(4)
     default: return set_error(ZI_ERR_ARG, "unsupported column layout");
   }
+#undef ZI_ELL_CASE
   ZI_LAUNCH_CHECK();
   return ZI_OK;
 }
@@ -1216,6 +1277,8 @@ struct CgPlan {
   const int32_t* colind;
   const int32_t* ell_ci = nullptr;  // FP32 ELL copy (null: CSR)
   const float* ell_va = nullptr;
+  const int32_t* ovf_ci = nullptr;  // overflow slots: the first eight tail entries of every row (or null)
+  const float* ovf_va = nullptr;
   const int32_t* tail_ptr = nullptr;
   const int32_t* tail_ci = nullptr;
   const float* tail_va = nullptr;
@@ -1255,13 +1318,13 @@ static int resident_grid(const void* fn, size_t smem, bool clustered, int cap) {
 }
 
 template <typename T>
-static const void* spmm_fn(int cptv, bool ell) {
+static const void* spmm_fn(int cptv, bool ell, bool ovf = false) {
   if constexpr (sizeof(T) == 4) {
     if (ell) {
       switch (cptv) {
-        case 1: return (const void*)k_spmm_ell<1>;
-        case 2: return (const void*)k_spmm_ell<2>;
-        case 4: return (const void*)k_spmm_ell<4>;
+        case 1: return ovf ? (const void*)k_spmm_ell<1, true> : (const void*)k_spmm_ell<1, false>;
+        case 2: return ovf ? (const void*)k_spmm_ell<2, true> : (const void*)k_spmm_ell<2, false>;
+        case 4: return ovf ? (const void*)k_spmm_ell<4, true> : (const void*)k_spmm_ell<4, false>;
       }
     }
   }
@@ -1295,11 +1358,11 @@ template <typename T>
 static void size_grids(CgPlan& p) {
   const bool ell = sizeof(T) == 4 && p.ell_ci && p.cptv <= 4;
   if (ell) {
-    p.smem_ell = ell_smem_bytes(p.tpr, p.ld);
-    (void)cudaFuncSetAttribute(spmm_fn<T>(p.cptv, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)p.smem_ell);
+    p.smem_ell = ell_smem_bytes(p.tpr, p.ld, p.ovf_ci != nullptr);
+    (void)cudaFuncSetAttribute(spmm_fn<T>(p.cptv, true, p.ovf_ci != nullptr),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem_ell);
   }
-  p.g_spmm = resident_grid(spmm_fn<T>(p.cptv, ell), ell ? p.smem_ell : p.smem, true, p.nblk);
+  p.g_spmm = resident_grid(spmm_fn<T>(p.cptv, ell, p.ovf_ci != nullptr), ell ? p.smem_ell : p.smem, true, p.nblk);
   p.g_resid = resident_grid(resid_fn<T>(p.cptv), p.smem, true, p.nblk);
   p.g_dir = resident_grid(dir_fn<T>(p.cptv), 0, false, 1 << 20);
 }
@@ -1311,8 +1374,8 @@ static int plan_spmm(const CgPlan& p, const T* vals, const T* P, T* Q, double* p
   if constexpr (sizeof(T) == 4) {
     // the FP32 operator is stored in difference form, which only the ELL kernel applies
     if (!p.ell_ci || p.cptv > 4) return set_error(ZI_ERR_ARG, "FP32 SpMM needs the ELL copy");
-    return launch_spmm_ell(p.cptv, dim3(p.g_spmm), p.tpr, p.smem_ell, st, p.n, p.ell_ci, p.ell_va, p.tail_ptr,
-                           p.tail_ci, p.tail_va, P, Q, p.ld, part, p.err, cnt, freeze);
+    return launch_spmm_ell(p.cptv, dim3(p.g_spmm), p.tpr, p.smem_ell, st, p.n, p.ell_ci, p.ell_va, p.ovf_ci,
+                           p.ovf_va, p.tail_ptr, p.tail_ci, p.tail_va, P, Q, p.ld, part, p.err, cnt, freeze);
   } else {
     return launch_spmm<T>(p.cptv, dim3(p.g_spmm), p.tpr, p.smem, st, p.n, p.rowptr, p.colind, vals, P, Q, p.ld,
                           part, cnt, freeze);
@@ -1590,8 +1653,11 @@ static int prepare_matrices(zi_system* S, const zi_solver_opts* o, cudaStream_t 
       ZI_CHECK(dalloc_n(&w->ell_va, (size_t)n * ELL_K, st));
     }
     DevTmp<int32_t> tcnt;
+    DevTmp<int> ntrows;
     ZI_CHECK(tcnt.alloc(n, st));
-    k_tail_count<<<grid_for(n, 256), 256, 0, st>>>(n, w->rowptr32, tcnt.p);
+    ZI_CHECK(ntrows.alloc(1, st));
+    ZI_CUDA(cudaMemsetAsync(ntrows.p, 0, sizeof(int), st));
+    k_tail_count<<<grid_for(n, 256), 256, 0, st>>>(n, w->rowptr32, tcnt.p, ntrows.p);
     ZI_LAUNCH_CHECK();
     DevTmp<int32_t> tptr;
     ZI_CHECK(tptr.alloc(n + 1, st));
@@ -1617,6 +1683,20 @@ static int prepare_matrices(zi_system* S, const zi_solver_opts* o, cudaStream_t 
     k_fill_ell<<<grid_for(n, 256), 256, 0, st>>>(n, w->rowptr32, w->colind32, w->v32, w->ell_ci, w->ell_va,
                                                  w->tail_ptr, w->tail_ci, w->tail_va);
     ZI_LAUNCH_CHECK();
+    // overflow slots when more than 5 % of the rows have a tail
+    int h_ntrows = 0;
+    ZI_CUDA(cudaMemcpyAsync(&h_ntrows, ntrows.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ZI_CUDA(cudaStreamSynchronize(st));
+    dfree(w->ovf_ci, st);
+    dfree(w->ovf_va, st);
+    w->ovf_ci = nullptr;
+    w->ovf_va = nullptr;
+    if (ntail > 0 && (int64_t)h_ntrows * 20 > n) {
+      ZI_CHECK(dalloc_n(&w->ovf_ci, (size_t)n * ELL_K, st));
+      ZI_CHECK(dalloc_n(&w->ovf_va, (size_t)n * ELL_K, st));
+      k_fill_ovf<<<grid_for(n, 256), 256, 0, st>>>(n, w->tail_ptr, w->tail_ci, w->tail_va, w->ovf_ci, w->ovf_va);
+      ZI_LAUNCH_CHECK();
+    }
     w->ntail = ntail;
     w->v32_ready = true;
   }
@@ -1649,6 +1729,8 @@ int head_begin(HeadRun& h) {
     h.p32.tail_ptr = w->tail_ptr;
     h.p32.tail_ci = w->tail_ci;
     h.p32.tail_va = w->tail_va;
+    h.p32.ovf_ci = w->ovf_ci;
+    h.p32.ovf_va = w->ovf_va;
     size_grids<float>(h.p32);
   }
   h.iters.assign(ld, 0);
@@ -1697,7 +1779,6 @@ int mixed_phase_begin(HeadRun& h) {
   const double tol2 = o->tol * o->tol;
   const double itol = o->inner_tol > 0 ? o->inner_tol : 5e-2;
   const int max_outer = o->max_outer > 0 ? o->max_outer : 30;
-  const size_t smem_init = sizeof(double) * (size_t)(BLOCK / ld) * ld;
   ZI_CUDA(cudaMemcpyAsync(w->gamma_prev, w->gamma, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st));
   k_flags_from_res<<<1, FIN_THREADS, 0, st>>>(ld, ncol, w->vec, w->bb, tol2, w->flag, w->gamma, w->nact);
   ZI_LAUNCH_CHECK();
@@ -2559,6 +2640,8 @@ extern "C" int zi_time_spmm(zi_system* S, int precision, int reps, double* ms_pe
     p.tail_ptr = w->tail_ptr;
     p.tail_ci = w->tail_ci;
     p.tail_va = w->tail_va;
+    p.ovf_ci = w->ovf_ci;
+    p.ovf_va = w->ovf_va;
     size_grids<float>(p);
   } else {
     size_grids<double>(p);
