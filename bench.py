@@ -39,7 +39,7 @@ WORKLOAD = "three-shell sphere 80/86/92 mm, h=2 mm Kuhn grid (428185 nodes, 2447
            "128 CEM electrodes r=5 mm z=2e-3 Ohm m^2, 20000 dipoles x 3, PCG tol 1e-10"
 # ncu DRAM traffic per launch of the FP32 SpMM on this workload, from the capture
 # summarised in profiles/ (None until taken, or once the kernel source changed).
-SPMM_TRAFFIC = {"source_sha": "488e651c6dd3ae69", "bytes": 246.936064e6 + 184.438272e6}
+SPMM_TRAFFIC = {"source_sha": "46c2569dbf4e86ad", "bytes": 246.94656e6 + 184.47488e6}
 
 
 def parse():
@@ -471,7 +471,7 @@ def main():
     achieved = bytes32 / (ms32 * 1e-3) / 1e9
     traffic = (SPMM_TRAFFIC["bytes"] if SPMM_TRAFFIC["source_sha"] == spmm_source_sha()
                and args.workload == "shell2mm" else None)
-    roofline = {"bound": "hbm", "kernel": "k_spmm_ell<1> (FP32 ELL SpMM fused with the p.q column dots)",
+    roofline = {"bound": "hbm", "kernel": "k_spmm_ell<1, false> (FP32 ELL SpMM fused with the p.q column dots)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_note": peak_note, "traffic": traffic, "algorithmic_bytes": bytes32,
                 "ms_per_launch": ms32}
