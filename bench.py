@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison build")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="shell2mm", choices=["shell2mm", "aniso1mm", "batch", "ias"],
+    ap.add_argument("--workload", default="shell2mm", choices=["shell2mm", "aniso1mm", "batch", "ias", "eit"],
                     help="shell2mm: the headline workload; aniso1mm: 1 mm anisotropic-skull head, 256 "
                          "electrodes, 100k dipoles; batch: 24 heads, batched vs per-head solves")
     return ap.parse_args()
@@ -372,6 +372,65 @@ def ias_workload(args):
 
 
 # ---------------------------------------------------------------------------
+# linearised EIT (App. A.3) on the 2 mm head with 32 electrodes
+# ---------------------------------------------------------------------------
+
+def eit_workload(args):
+    """The EIT Jacobian of 31 adjacent-pair patterns on all 32 electrodes for
+    every tet of the 2 mm head (m x 31 x 32, 19.4 GB written) and its VJP,
+    from the head's transfer matrix (solved once, not timed)."""
+    import torch
+    from paper_1811_07717_gb300 import workloads as W
+    from paper_1811_07717_gb300 import _build, zi
+    _build.build()
+    spec = W.config_eit_2mm()
+    mesh = zi.mesh_from_grid(spec.h, spec.radii)
+    s6 = W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(),
+                        mesh["labels"].cpu().numpy())
+    centres, z = W.electrode_inputs(spec)
+    system = zi.System(mesh["nodes"], mesh["tets"], s6, mesh["bfaces"], centres, model="cem", z=z,
+                       radius=spec.electrode_radius)
+    opts = zi.SolverOpts(tol=1e-10)
+    system.transfer(opts)
+    I = torch.from_numpy(W.injection_patterns(spec.n_electrodes)).cuda()
+    gy = torch.ones((I.shape[0], spec.n_electrodes), dtype=torch.float64, device="cuda")
+    m = system.info()["m"]
+
+    def timed(mode, reps):
+        system.eit(I, mode=mode, grad_y=gy if mode == zi.EIT_VJP else None, opts=opts, want_y=False)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record()
+        for _ in range(reps):
+            _, out = system.eit(I, mode=mode, grad_y=gy if mode == zi.EIT_VJP else None, opts=opts, want_y=False)
+            del out
+        t1.record()
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3 / reps
+
+    with Clocks(torch.cuda.current_device()) as clk:
+        vjp = timed(zi.EIT_VJP, max(1, args.steps))
+        full = timed(zi.EIT_FULL, max(1, args.steps))
+    system.close()
+    out_bytes = float(m) * I.shape[0] * spec.n_electrodes * 8
+    L_el, n_pat = spec.n_electrodes, I.shape[0]
+    flops = float(m) * 2.0 * L_el * (16 + 4 * n_pat)  # K w_k per electrode, then u_p . (K w_k)
+    peak_tf = 1.25  # nominal FP64 rate of the part (no measured FP64 figure is available)
+    line = {"metric": "linearised-EIT Jacobian s (31 patterns x 32 electrodes x every tet, 2 mm head)",
+            "value": full, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+            "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "three-shell 2 mm head, 32 CEM electrodes, 31 adjacent-pair 1 mA patterns",
+                       "tets": int(m), "jacobian_bytes": out_bytes},
+            "vjp_s": vjp,
+            "roofline": {"bound": "alu", "kernel": "k_eit_full (FP64: -u_p^T K_m w_k for every tet)",
+                         "achieved": flops / full / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": flops / full / 1e12 / peak_tf, "peak_note": "nominal FP64", "traffic": None,
+                         "jacobian_write_GBps": out_bytes / full / 1e9},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -397,6 +456,8 @@ def main():
         return batch_workload(args)
     if args.workload == "ias":
         return ias_workload(args)
+    if args.workload == "eit":
+        return eit_workload(args)
     spec = W.config_three_shell_2mm() if args.workload == "shell2mm" else W.config_three_shell_1mm_aniso()
     workload = WORKLOAD if args.workload == "shell2mm" else (
         "three-shell sphere 80/86/92 mm, h=1 mm Kuhn grid (3342701 nodes, 19573872 tets), transversely "
