@@ -559,3 +559,45 @@ def test_assembled_couplings_are_noise_or_genuine():
         assert noise.sum() > 0.3 * off.sum()            # the diagonal edges are there
         assert np.all(rel[noise] < 1e-14)               # and at rounding level
         assert np.all(rel[~noise] > 2.0 ** -24)         # everything else survives both cuts
+
+
+def test_difference_form_operator_is_the_matrix():
+    """Reading P20: the inner FP32 solve applies A as c_i p_i + sum_{j != i}
+    a_ij (p_j - p_i) with c_i the row sum.  In exact arithmetic that is A p
+    (checked here in FP64 on the oracle's assembled CEM matrix), and in FP32
+    it is far closer to A p than the plain form on a smooth vector."""
+    spec = W.three_shell(0.006, 16, 10, seed=2, skull_aniso=(0.00132, 0.0132))
+    mesh = O.mesh_from_grid(spec.h, spec.radii)
+    s6 = W.conductivity(spec, mesh["nodes"], mesh["tets"], mesh["labels"])
+    centres, z = W.electrode_inputs(spec)
+    system = O.System(mesh, s6, centres, spec.electrode_model, radius=spec.electrode_radius, z=z)
+    A = system.A.tocoo()
+    c = np.asarray(system.A.sum(axis=1)).ravel()
+    off = A.row != A.col
+
+    def diff_form(p, dtype):
+        a = A.data[off].astype(dtype)
+        t = a * (p[A.col[off]].astype(dtype) - p[A.row[off]].astype(dtype))
+        q = np.zeros(A.shape[0], dtype=dtype)
+        np.add.at(q, A.row[off], t)
+        return q + c.astype(dtype) * p.astype(dtype)
+
+    rng = np.random.default_rng(0)
+    p = rng.standard_normal(A.shape[0])
+    exact = system.A @ p
+    assert np.linalg.norm(diff_form(p, np.float64) - exact) <= 1e-12 * np.linalg.norm(exact)
+    # a smooth vector (a linear function plus a constant), stored in FP32 as the inner solve stores its
+    # direction; the exact product is A applied to that stored vector.  On the stiffness rows a linear
+    # function lies in the kernel of A, so A p cancels in the plain form but not in the difference form.
+    x = mesh["nodes"]
+    ps = (1.0 + 0.3 * x[:, 0] / 0.092 + 0.2 * x[:, 2] / 0.092).astype(np.float32).astype(np.float64)
+    ex = system.A @ ps
+    plain = (system.A.astype(np.float32) @ ps.astype(np.float32)).astype(np.float64)
+    diff = diff_form(ps, np.float32).astype(np.float64)
+    scale = abs(system.A) @ np.abs(ps)
+    interior = np.abs(ex) < 1e-6 * scale
+    assert interior.sum() > A.shape[0] // 4
+    err_plain = np.abs(plain - ex)
+    err_diff = np.abs(diff - ex)
+    assert np.linalg.norm(err_diff) < 0.2 * np.linalg.norm(err_plain)
+    assert np.linalg.norm(err_diff[interior]) < 0.02 * np.linalg.norm(err_plain[interior])
