@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison build")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="shell2mm", choices=["shell2mm", "aniso1mm", "batch", "ias", "eit"],
+    ap.add_argument("--workload", default="shell2mm", choices=["shell2mm", "aniso1mm", "batch", "ias", "eit", "hdiv"],
                     help="shell2mm: the headline workload; aniso1mm: 1 mm anisotropic-skull head, 256 "
                          "electrodes, 100k dipoles; batch: 24 heads, batched vs per-head solves")
     return ap.parse_args()
@@ -430,6 +430,73 @@ def eit_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def hdiv_workload(args):
+    """The 2 mm lead-field build with Cartesian H(div) sources (PBO 10-source
+    stencil, Sec. 2.1) in place of partial integration: the whole build, and
+    the two source steps alone (stencil construction; T^T F and the electrode
+    step) next to the partial-integration source step."""
+    import torch
+    from paper_1811_07717_gb300 import workloads as W
+    from paper_1811_07717_gb300 import _build, zi
+    _build.build()
+    spec = W.config_three_shell_2mm()
+    mesh = zi.mesh_from_grid(spec.h, spec.radii)
+    s6 = torch.from_numpy(W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(),
+                                         mesh["labels"].cpu().numpy())).cuda()
+    centres, z = W.electrode_inputs(spec)
+    centres, z = torch.from_numpy(centres).cuda(), torch.from_numpy(z).cuda()
+    pos = torch.from_numpy(W.dipole_inputs(spec)[0]).cuda()
+    mixed = zi.SolverOpts(tol=1e-10, precision=zi.MIXED)
+
+    def build_system():
+        return zi.System(mesh["nodes"], mesh["tets"], s6, mesh["bfaces"], centres, model="cem", z=z,
+                         radius=spec.electrode_radius)
+
+    def lf_build():
+        dip = zi.locate_dipoles_grid(spec.h, spec.radii, pos)
+        system = build_system()
+        L = system.leadfield_hdiv(pos, dip, zi.SOURCE_PBO10, opts=mixed)
+        system.close()
+        return L
+
+    def ev_time(fn, reps):
+        fn()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record()
+        for _ in range(reps):
+            fn()
+        t1.record()
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3 / reps
+
+    for _ in range(args.warmup):
+        lf_build()
+    torch.cuda.synchronize()
+    l0 = zi.kernel_launches()
+    with Clocks(torch.cuda.current_device()) as clk:
+        sec = ev_time(lf_build, max(1, args.steps))
+    launches = (zi.kernel_launches() - l0) // (max(1, args.steps) + 1)
+    system = build_system()
+    system.transfer(mixed, want_T=False)
+    dip = zi.locate_dipoles_grid(spec.h, spec.radii, pos)
+    Fn, Fw = system.source_stencil(pos, dip, zi.SOURCE_PBO10)
+    t_stencil = ev_time(lambda: system.source_stencil(pos, dip, zi.SOURCE_PBO10), 5)
+    t_sparse = ev_time(lambda: system.leadfield_sparse(Fn, Fw, mixed), 5)
+    t_pi = ev_time(lambda: system.leadfield(dip, mixed), 5)
+    system.close()
+    line = {"metric": "EEG lead-field build s, Cartesian H(div) sources (PBO 10-source stencil)",
+            "value": sec, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "dtype": "f32 inner PCG / f64 refinement, assembly, LF",
+            "data": "synthetic",
+            "config": {"workload": "three-shell 2 mm head (428185 nodes, 2447424 tets), 128 CEM electrodes, "
+                                   "20000 H(div) sources x 3 orientations, PCG tol 1e-10, mixed precision"},
+            "source_stencil_s": t_stencil, "leadfield_sparse_s": t_sparse,
+            "leadfield_partial_integration_s": t_pi,
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -458,6 +525,8 @@ def main():
         return ias_workload(args)
     if args.workload == "eit":
         return eit_workload(args)
+    if args.workload == "hdiv":
+        return hdiv_workload(args)
     spec = W.config_three_shell_2mm() if args.workload == "shell2mm" else W.config_three_shell_1mm_aniso()
     workload = WORKLOAD if args.workload == "shell2mm" else (
         "three-shell sphere 80/86/92 mm, h=1 mm Kuhn grid (3342701 nodes, 19573872 tets), transversely "

@@ -235,6 +235,55 @@ int zi_leadfield(zi_system* sys, const int32_t* dip_tet, int64_t P,
                  const zi_solver_opts* opts, double* L, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* H(div) sources (Sec. 2.1, primary current model)                            */
+/* ------------------------------------------------------------------------ */
+
+/* Source stencils: the four face functions of the holding tet (Whitney), or
+ * those plus its six edge functions (the 10-source stencil). */
+enum { ZI_SOURCE_WHITNEY4 = 0, ZI_SOURCE_PBO10 = 1 };
+#define ZI_STENCIL_WIDTH 8          /* entries per source-matrix column */
+#define ZI_PBO_LAMBDA_DEFAULT 1e-2  /* Tikhonov weight of the PBO fit */
+
+/* Columns of the source matrix F for Cartesian H(div) sources at positions
+ * pos (device P x 3 f64, m) in tets dip_tet (device P i32).  Column 3p + j
+ * (orientation e_j, Sec. 2.5 ordering) is sum_k w_k f_k over the stencil of
+ * tet t = dip_tet[p]:
+ *   face source k: the lowest-order Raviart-Thomas function of the face
+ *     opposite vertex v_k with unit flux into the neighbour N_k; load
+ *     (e_{o_k} - e_{v_k})/4 (o_k: N_k's vertex off the face), moment
+ *     (x_{o_k} - x_{v_k})/4 at the face centroid; absent on the mesh boundary;
+ *   edge source (a, b) (ZI_SOURCE_PBO10): load e_{v_b} - e_{v_a}, moment
+ *     x_{v_b} - x_{v_a} at the edge midpoint.
+ * Position-based optimisation: w minimises the first moment of the combined
+ * source about x0, |sum_k w_k d_k (c_k - x0)^T / s|_F^2, plus
+ * lambda sum_k (1 + |c_k - x0|^2/s^2) |d_k|^2 w_k^2 (s: mean edge length of t),
+ * subject to sum_k w_k d_k = e_j (the dipole moment exactly).
+ *   lambda: > 0, or 0 for ZI_PBO_LAMBDA_DEFAULT.
+ *   F_nodes: device out, 3P x ZI_STENCIL_WIDTH i32: t's four vertices, then
+ *     the vertex across each face (t's own vertex where the face is on the
+ *     boundary, with weight 0).
+ *   F_w: device out, 3P x ZI_STENCIL_WIDTH f64, the loads at those nodes.
+ * Feed both to zi_leadfield_sparse.  Scratch: a node -> tet incidence list
+ * (4m + n + 1 int32).  ZI_ERR_BAD_MESH for a tet index outside the mesh, a face
+ * shared by more than two tets, or a stencil whose moments do not span R^3
+ * (a Whitney stencil with two boundary faces); that column's weights are 0.
+ * Synchronises. */
+int zi_source_stencil(zi_system* sys, const double* pos, const int32_t* dip_tet, int64_t P, int model,
+                      double lambda, int32_t* F_nodes, double* F_w, cudaStream_t stream);
+
+/* L for a source matrix F given column by column: column c has the load
+ * F_w[c*K + j] at node F_nodes[c*K + j], j < K (repeated nodes add up).
+ * L = R (C - B^T T)^-1 T^T F (CEM) or T^T F (point electrodes), as in
+ * zi_leadfield, with ncols columns.
+ *   F_nodes: device in, ncols x K i32; F_w: device in, ncols x K f64; 1 <= K <= 32.
+ *   L: device out, n_rows_L x ncols f64.
+ * ZI_ERR_ARG for a node index outside the mesh or a non-finite weight (L is
+ * not written).  Runs zi_transfer with opts first if the handle holds no T.
+ * Synchronises. */
+int zi_leadfield_sparse(zi_system* sys, const int32_t* F_nodes, const double* F_w, int64_t ncols, int K,
+                        const zi_solver_opts* opts, double* L, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Linearised EIT (App. A.3)                                                   */
 /* ------------------------------------------------------------------------ */
 

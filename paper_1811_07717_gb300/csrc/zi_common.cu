@@ -52,6 +52,12 @@ int device_error_to_status(int d) {
   if (d & DEV_ERR_VALENCE) return set_error(ZI_ERR_BAD_MESH, "node valence above the supported bound");
   if (d & DEV_ERR_NO_GROUND) return set_error(ZI_ERR_BAD_MESH, "no boundary node outside the electrodes");
   if (d & DEV_ERR_NOT_SPD) return set_error(ZI_ERR_BAD_MESH, "electrode Schur matrix is not positive definite");
+  if (d & DEV_ERR_NONMANIFOLD) return set_error(ZI_ERR_BAD_MESH, "a face is shared by more than two elements");
+  if (d & DEV_ERR_STENCIL)
+    return set_error(ZI_ERR_BAD_MESH, "a source stencil cannot represent all three orientations");
+  if (d & DEV_ERR_BAD_INDEX)
+    return set_error(ZI_ERR_ARG, "node index outside the mesh (a source-matrix entry or an element vertex) or a "
+                     "non-finite source weight");
   if (d & DEV_ERR_TIMEOUT) return set_error(ZI_ERR_TIMEOUT, "device-side wait exceeded its bound");
   return set_error(ZI_ERR_CUDA, "device error word 0x%x", d);
 }

@@ -56,6 +56,9 @@ enum : int {
   DEV_ERR_NO_PATCH = 128,
   DEV_ERR_NO_GROUND = 256,
   DEV_ERR_NOT_SPD = 512,
+  DEV_ERR_NONMANIFOLD = 1024,
+  DEV_ERR_STENCIL = 2048,
+  DEV_ERR_BAD_INDEX = 4096,
 };
 
 int device_error_to_status(int dev_err);
@@ -144,6 +147,9 @@ void system_free(zi_system* s);
 
 // Helpers implemented in zi_pcg.cu / zi_leadfield.cu used across units.
 int schur_matrix(zi_system* sys, double* S, cudaStream_t s);  // S = C - B^T T (L x L)
+// L = R S^-1 H (CEM) or H (point electrodes) from Ht = (T^T F)^T, N x n_rhs;
+// synchronises the stream.
+int leadfield_finish(zi_system* sys, const double* Ht, int64_t N, double* Lout, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // device helpers

@@ -68,6 +68,40 @@ __global__ void k_source_apply(int64_t P, const int32_t* __restrict__ dip_tet, i
   }
 }
 
+// Ht[c][l] = sum_j Fw[c][j] * T[Fn[c][j]][l]: a source matrix F given column
+// by column with K stored entries each (the H(div) stencils of
+// zi_source_stencil, or any caller's F).  One warp per column; lane j < K
+// holds entry j and broadcasts it, lanes then run over the columns of T.
+__global__ void k_source_apply_ell(int64_t ncols, int K, const int32_t* __restrict__ Fn,
+                                   const double* __restrict__ Fw, int64_t n, const double* __restrict__ T,
+                                   int ncol, double* __restrict__ Ht, int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < ncols; c += warps) {
+    int32_t node = 0;
+    double w = 0.0;
+    if (lane < K) {
+      node = Fn[c * K + lane];
+      w = Fw[c * K + lane];
+    }
+    const bool bad = lane < K && (node < 0 || node >= n || !isfinite(w));
+    if (__any_sync(0xffffffffu, bad)) {
+      if (lane == 0) atomicOr(err, DEV_ERR_BAD_INDEX);
+      for (int l = lane; l < ncol; l += 32) Ht[c * ncol + l] = 0.0;
+      continue;
+    }
+    for (int l = lane; l < ncol; l += 32) {
+      double h = 0.0;
+      for (int j = 0; j < K; ++j) {
+        const int32_t nj = __shfl_sync(0xffffffffu, node, j);
+        const double wj = __shfl_sync(0xffffffffu, w, j);
+        h = fma(wj, T[(int64_t)nj * ncol + l], h);
+      }
+      Ht[c * ncol + l] = h;
+    }
+  }
+}
+
 // S[k][l] = C_k delta_kl - sum over patch nodes i (ascending) of B[i][k] T[i][l].
 // S = C - B^T T over the patch nodes (App. A.2).  Column k of B is nonzero
 // only on electrode k's patch nodes, so block k first compacts, in node
@@ -291,7 +325,27 @@ int leadfield_impl(zi_system* S, const int32_t* dip_tet, int64_t P, double* Lout
                                                                   Ht.p, err.p);
   ZI_LAUNCH_CHECK();
   ZI_CHECK(read_dev_err(err.p, s));
-  const int64_t N = 3 * P;
+  return leadfield_finish(S, Ht.p, 3 * P, Lout, s);
+}
+
+int leadfield_sparse_impl(zi_system* S, const int32_t* Fn, const double* Fw, int64_t ncols, int K, double* Lout,
+                          cudaStream_t s) {
+  const int ncol = S->n_rhs;
+  DevTmp<double> Ht;
+  DevTmp<int> err;
+  ZI_CHECK(Ht.alloc((size_t)ncols * ncol, s));
+  ZI_CHECK(err.alloc(1, s));
+  ZI_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  k_source_apply_ell<<<grid_for(ncols * 32, 256, 152u * 64u), 256, 0, s>>>(ncols, K, Fn, Fw, S->n, S->T, ncol,
+                                                                          Ht.p, err.p);
+  ZI_LAUNCH_CHECK();
+  ZI_CHECK(read_dev_err(err.p, s));
+  return leadfield_finish(S, Ht.p, ncols, Lout, s);
+}
+
+// L from Ht = (T^T F)^T (N x n_rhs): L = R S^-1 H (CEM) or H (point electrodes).
+int leadfield_finish(zi_system* S, const double* Ht, int64_t N, double* Lout, cudaStream_t s) {
+  const int ncol = S->n_rhs;
   if (S->model == ZI_ELECTRODE_CEM) {
     const int L = S->n_el;
     DevTmp<double> Sm, Wm;
@@ -300,11 +354,11 @@ int leadfield_impl(zi_system* S, const int32_t* dip_tet, int64_t P, double* Lout
     ZI_CHECK(schur_matrix(S, Sm.p, s));
     ZI_CHECK(schur_inverse(S, Sm.p, Wm.p, 1, s));
     dim3 grid((unsigned)((N + GT - 1) / GT), (unsigned)((L + GT - 1) / GT));
-    k_gemm_abt<<<grid, 256, 0, s>>>(L, L, N, Wm.p, Ht.p, Lout);
+    k_gemm_abt<<<grid, 256, 0, s>>>(L, L, N, Wm.p, Ht, Lout);
     ZI_LAUNCH_CHECK();
   } else {
     dim3 grid((unsigned)((N + 31) / 32), (unsigned)((ncol + 31) / 32));
-    k_transpose<<<grid, dim3(32, 8), 0, s>>>(ncol, N, Ht.p, Lout);
+    k_transpose<<<grid, dim3(32, 8), 0, s>>>(ncol, N, Ht, Lout);
     ZI_LAUNCH_CHECK();
   }
   ZI_CUDA(cudaStreamSynchronize(s));
@@ -331,6 +385,25 @@ extern "C" int zi_leadfield(zi_system* S, const int32_t* dip_tet, int64_t P, con
   }
   if (P == 0) return ZI_OK;
   return leadfield_impl(S, dip_tet, P, L, s);
+}
+
+extern "C" int zi_leadfield_sparse(zi_system* S, const int32_t* F_nodes, const double* F_w, int64_t ncols, int K,
+                                   const zi_solver_opts* o, double* L, cudaStream_t s) {
+  if (!S) return set_error(ZI_ERR_ARG, "null system");
+  if (ncols < 0) return set_error(ZI_ERR_ARG, "negative column count");
+  if (K < 1 || K > 32) return set_error(ZI_ERR_ARG, "entries per column must be in 1..32 (got %d)", K);
+  if (ncols > 0 && (!F_nodes || !F_w || !L)) return set_error(ZI_ERR_ARG, "null source or output array");
+  if (!S->has_T) {
+    ZI_CHECK(check_opts(o));
+    int st = transfer_impl(S, o, nullptr, nullptr, nullptr, s);
+    if (st != ZI_OK && st != ZI_ERR_NOT_CONVERGED) return st;
+    if (st == ZI_ERR_NOT_CONVERGED) {
+      if (ncols > 0) ZI_CHECK(leadfield_sparse_impl(S, F_nodes, F_w, ncols, K, L, s));
+      return set_error(ZI_ERR_NOT_CONVERGED, "transfer solve did not reach tol; L written from the last iterate");
+    }
+  }
+  if (ncols == 0) return ZI_OK;
+  return leadfield_sparse_impl(S, F_nodes, F_w, ncols, K, L, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -23,13 +23,15 @@ PRECOND_JACOBI, PRECOND_LDP = 0, 1
 FP64, MIXED = 0, 1
 EIT_FULL, EIT_VJP = 0, 1
 HYPER_G, HYPER_IG = 0, 1
+SOURCE_WHITNEY4, SOURCE_PBO10 = 0, 1
+STENCIL_WIDTH = 8
 
 # Every symbol include/zi.h declares.
 EXPORTS = ("zi_version", "zi_last_error", "zi_status_string", "zi_mesh_from_grid",
            "zi_locate_dipoles_grid", "zi_assemble", "zi_system_set_conductivity",
            "zi_system_get_info", "zi_system_get_matrix", "zi_system_destroy",
            "zi_solver_opts_default", "zi_transfer", "zi_transfer_batched", "zi_leadfield",
-           "zi_eit_jacobian", "zi_leadfield_noalloc", "zi_ias_map", "zi_time_spmm", "zi_kernel_launches")
+           "zi_source_stencil", "zi_leadfield_sparse", "zi_eit_jacobian", "zi_leadfield_noalloc", "zi_ias_map", "zi_time_spmm", "zi_kernel_launches")
 
 
 class ZiError(RuntimeError):
@@ -88,6 +90,8 @@ def load_library(path: str = LIB_PATH):
         "zi_transfer": ([P, ctypes.POINTER(_Opts), P, P, P, P], ctypes.c_int),
         "zi_transfer_batched": ([P, ctypes.c_int, ctypes.POINTER(_Opts), P, P, P], ctypes.c_int),
         "zi_leadfield": ([P, P, I64, ctypes.POINTER(_Opts), P, P], ctypes.c_int),
+        "zi_source_stencil": ([P, P, P, I64, ctypes.c_int, D, P, P, P], ctypes.c_int),
+        "zi_leadfield_sparse": ([P, P, P, I64, ctypes.c_int, ctypes.POINTER(_Opts), P, P], ctypes.c_int),
         "zi_eit_jacobian": ([P, P, ctypes.c_int, ctypes.c_int, P, P, P, ctypes.POINTER(_Opts), P], ctypes.c_int),
         "zi_leadfield_noalloc": ([P, P, I64, P, P], ctypes.c_int),
         "zi_ias_map": ([P, I32, I64, P, I32, D, D, D, I32, I32, P, P, P], ctypes.c_int),
@@ -293,6 +297,46 @@ class System:
         o = opts.c()
         _check(self._lib.zi_leadfield(self._h, _ptr(dt), P, ctypes.byref(o), _ptr(L), _stream()))
         return L
+
+    def source_stencil(self, pos, dip_tet, model=SOURCE_PBO10, lam: float = 0.0):
+        """Source-matrix columns of Cartesian H(div) sources (zi_source_stencil):
+        returns (F_nodes, F_w), each 3P x STENCIL_WIDTH; positions in metres."""
+        torch = _torch()
+        ps = _dev(pos, torch.float64).reshape(-1, 3).contiguous()
+        dt = _dev(dip_tet, torch.int32)
+        P = dt.shape[0]
+        if ps.shape[0] != P:
+            raise ValueError("pos and dip_tet disagree on the source count")
+        Fn = torch.empty((3 * P, STENCIL_WIDTH), dtype=torch.int32, device=self.nodes.device)
+        Fw = torch.empty((3 * P, STENCIL_WIDTH), dtype=torch.float64, device=self.nodes.device)
+        _check(self._lib.zi_source_stencil(self._h, _ptr(ps), _ptr(dt), P, int(model), float(lam), _ptr(Fn),
+                                           _ptr(Fw), _stream()))
+        return Fn, Fw
+
+    def leadfield_sparse(self, F_nodes, F_w, opts: SolverOpts | None = None, out=None):
+        """L (zi_leadfield_sparse) for a source matrix given column by column
+        (ncols x K node indices and loads)."""
+        torch = _torch()
+        opts = opts or SolverOpts()
+        Fn = _dev(F_nodes, torch.int32).contiguous()
+        Fw = _dev(F_w, torch.float64).contiguous()
+        if Fn.dim() != 2 or Fn.shape != Fw.shape:
+            raise ValueError("F_nodes and F_w must both be ncols x K")
+        ncols, K = Fn.shape
+        inf = self.info()
+        L = out if out is not None else torch.empty((inf["n_rows_L"], ncols), dtype=torch.float64,
+                                                    device=self.nodes.device)
+        o = opts.c()
+        _check(self._lib.zi_leadfield_sparse(self._h, _ptr(Fn), _ptr(Fw), ncols, K, ctypes.byref(o), _ptr(L),
+                                             _stream()))
+        return L
+
+    def leadfield_hdiv(self, pos, dip_tet, model=SOURCE_PBO10, lam: float = 0.0,
+                       opts: SolverOpts | None = None):
+        """L for Cartesian H(div) sources (Sec. 2.1): the stencil columns, then
+        the sparse lead field; columns 3p + d as in leadfield()."""
+        Fn, Fw = self.source_stencil(pos, dip_tet, model, lam)
+        return self.leadfield_sparse(Fn, Fw, opts)
 
     def eit(self, I, mode=EIT_FULL, grad_y=None, opts: SolverOpts | None = None, want_y=True):
         """Linearised EIT (zi_eit_jacobian): returns (y, out)."""
