@@ -65,3 +65,37 @@ def sphere_dipole_potential(r, r0, q, sigma: float, R: float, nterms: int = 400)
         dP_prev, dP_cur = dP_cur, dP_next
         scale = scale * x
     return u_inf + u_c / (4.0 * math.pi * sigma)
+
+
+MU0_OVER_4PI = 1e-7  # T m / A
+
+
+def sarvas_field(r, r0, q) -> np.ndarray:
+    """Magnetic field outside a spherically symmetric conductor centred at the
+    origin, at points r (k,3), of a current dipole q (3,) at r0 (3,) inside it
+    (Sarvas' closed form, which follows from B = -mu0 grad U outside the
+    conductor and the radial component being that of the primary current
+    alone):
+        a = r - r0,  F = |a| (|r||a| + |r|^2 - r0.r),
+        grad F = (|a|^2/|r| + a.r/|a| + 2|a| + 2|r|) r - (|a| + 2|r| + a.r/|a|) r0,
+        B = mu0/(4 pi F^2) (F q x r0 - ((q x r0).r) grad F).
+    Independent of the radial conductivity profile."""
+    r = np.atleast_2d(np.asarray(r, dtype=np.float64))
+    r0 = np.asarray(r0, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    a = r - r0
+    an = np.linalg.norm(a, axis=1)
+    rn = np.linalg.norm(r, axis=1)
+    ar = np.sum(a * r, axis=1)
+    F = an * (rn * an + rn * rn - r @ r0)
+    gF = ((an * an / rn + ar / an + 2.0 * an + 2.0 * rn)[:, None] * r
+          - (an + 2.0 * rn + ar / an)[:, None] * r0[None, :])
+    qx = np.cross(q, r0)
+    return MU0_OVER_4PI / (F * F)[:, None] * (F[:, None] * qx[None, :] - (r @ qx)[:, None] * gF)
+
+
+def primary_field(r, r0, q) -> np.ndarray:
+    """Biot-Savart field of the primary current alone, mu0/(4 pi) q x (r - r0)/|r - r0|^3."""
+    r = np.atleast_2d(np.asarray(r, dtype=np.float64))
+    a = r - np.asarray(r0, dtype=np.float64)
+    return MU0_OVER_4PI * np.cross(np.asarray(q, dtype=np.float64), a) / np.linalg.norm(a, axis=1)[:, None] ** 3

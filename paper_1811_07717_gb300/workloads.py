@@ -196,3 +196,18 @@ def injection_patterns(n_electrodes: int, amplitude: float = 1e-3) -> np.ndarray
         I[p, p] = amplitude
         I[p, p + 1] = -amplitude
     return I
+
+
+def meg_sensors(n: int, radius: float, tilt: float = 0.6):
+    """n magnetometers on the golden-angle spiral at the given radius, unit
+    orientation radial + tilt * (a tangential direction), normalised.  The
+    tilt gives every sensor a tangential component, which the volume
+    currents of a spherical head do reach."""
+    pos = fibonacci_points(n, radius)
+    rhat = pos / np.linalg.norm(pos, axis=1, keepdims=True)
+    ref = np.where(np.abs(rhat[:, 2:3]) < 0.9, np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]]))
+    t = np.cross(ref, rhat)
+    t /= np.linalg.norm(t, axis=1, keepdims=True)
+    d = rhat + tilt * t
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return np.ascontiguousarray(pos), np.ascontiguousarray(d)
