@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison build")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="shell2mm", choices=["shell2mm", "aniso1mm", "batch", "ias", "eit", "hdiv"],
+    ap.add_argument("--workload", default="shell2mm", choices=["shell2mm", "aniso1mm", "batch", "ias", "eit", "hdiv", "meg"],
                     help="shell2mm: the headline workload; aniso1mm: 1 mm anisotropic-skull head, 256 "
                          "electrodes, 100k dipoles; batch: 24 heads, batched vs per-head solves")
     return ap.parse_args()
@@ -497,6 +497,79 @@ def hdiv_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def meg_workload(args):
+    """The MEG lead field of the 2 mm head (App. A.2 by Biot-Savart): 256
+    magnetometers 20 mm outside the scalp, 20,000 partial-integration dipoles
+    x 3; the build = assembly, the sensors' right-hand sides, one mixed
+    precision PCG solve per sensor, the source columns and L."""
+    import torch
+    from paper_1811_07717_gb300 import workloads as W
+    from paper_1811_07717_gb300 import _build, zi
+    _build.build()
+    spec = W.config_three_shell_2mm()
+    mesh = zi.mesh_from_grid(spec.h, spec.radii)
+    s6 = torch.from_numpy(W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(),
+                                         mesh["labels"].cpu().numpy())).cuda()
+    centres, z = W.electrode_inputs(spec)
+    centres, z = torch.from_numpy(centres).cuda(), torch.from_numpy(z).cuda()
+    pos = torch.from_numpy(W.dipole_inputs(spec)[0]).cuda()
+    sp_np, sd_np = W.meg_sensors(256, spec.radii[-1] + 0.02)
+    sp_, sd = torch.from_numpy(sp_np).cuda(), torch.from_numpy(sd_np).cuda()
+    mixed = zi.SolverOpts(tol=1e-10, precision=zi.MIXED)
+
+    def build_system():
+        return zi.System(mesh["nodes"], mesh["tets"], s6, mesh["bfaces"], centres, model="cem", z=z,
+                         radius=spec.electrode_radius)
+
+    def lf_build():
+        dip = zi.locate_dipoles_grid(spec.h, spec.radii, pos)
+        system = build_system()
+        Tm, _, _ = system.meg_transfer(sp_, sd, mixed)
+        Fn, Fw = system.source_pi(dip)
+        L = system.meg_leadfield(Tm, sp_, sd, pos, Fn, Fw)
+        system.close()
+        return L
+
+    def ev_time(fn, reps):
+        fn()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record()
+        for _ in range(reps):
+            fn()
+        t1.record()
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3 / reps
+
+    for _ in range(args.warmup):
+        lf_build()
+    torch.cuda.synchronize()
+    l0 = zi.kernel_launches()
+    with Clocks(torch.cuda.current_device()) as clk:
+        sec = ev_time(lf_build, max(1, args.steps))
+    launches = (zi.kernel_launches() - l0) // (max(1, args.steps) + 1)
+    system = build_system()
+    t_rhs = ev_time(lambda: system.meg_rhs(sp_, sd), 3)
+    _, it, rr = system.meg_transfer(sp_, sd, mixed)
+    system.close()
+    m = int(mesh["tets"].shape[0])
+    flops = 180.0 * m * 256  # per (tet, sensor): gradients, 4-point kernel integral, cross and sigma products
+    peak_tf = 1.25
+    line = {"metric": "MEG lead-field build s (Biot-Savart, 256 magnetometers)", "value": sec, "unit": "s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "dtype": "f64 right-hand sides and L; f32 inner PCG / f64 refinement", "data": "synthetic",
+            "config": {"workload": "three-shell 2 mm head (428185 nodes, 2447424 tets), 128 CEM electrodes "
+                                   "attached, 256 magnetometers on a 112 mm sphere (radial + 0.6 tangential), "
+                                   "20000 dipoles x 3, PCG tol 1e-10, mixed precision"},
+            "meg_rhs_s": t_rhs, "iterations_max": int(it.max()), "relres_max": float(rr.max()),
+            "roofline": {"bound": "alu", "kernel": "k_meg_tet (FP64 kernel integrals per tet and sensor)",
+                         "achieved": flops / t_rhs / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": flops / t_rhs / 1e12 / peak_tf, "peak_note": "nominal FP64; the right-hand "
+                         "side build (both of its kernels) timed", "traffic": None},
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -527,6 +600,8 @@ def main():
         return eit_workload(args)
     if args.workload == "hdiv":
         return hdiv_workload(args)
+    if args.workload == "meg":
+        return meg_workload(args)
     spec = W.config_three_shell_2mm() if args.workload == "shell2mm" else W.config_three_shell_1mm_aniso()
     workload = WORKLOAD if args.workload == "shell2mm" else (
         "three-shell sphere 80/86/92 mm, h=1 mm Kuhn grid (3342701 nodes, 19573872 tets), transversely "

@@ -283,6 +283,53 @@ int zi_source_stencil(zi_system* sys, const double* pos, const int32_t* dip_tet,
 int zi_leadfield_sparse(zi_system* sys, const int32_t* F_nodes, const double* F_w, int64_t ncols, int K,
                         const zi_solver_opts* opts, double* L, cudaStream_t stream);
 
+/* Partial-integration source columns in the form zi_leadfield_sparse and
+ * zi_meg_leadfield take: column 3p + d holds d psi_a / d x_d at the four
+ * vertices a of tet dip_tet[p] (the same F as zi_leadfield).
+ *   F_nodes: device out, 3P x 4 i32; F_w: device out, 3P x 4 f64.
+ * ZI_ERR_BAD_MESH for a tet index outside the mesh.  Synchronises. */
+int zi_source_pi(zi_system* sys, const int32_t* dip_tet, int64_t P, int32_t* F_nodes, double* F_w,
+                 cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* MEG lead field (App. A.2: the Biot-Savart formula)                          */
+/* ------------------------------------------------------------------------ */
+
+/* Magnetometers at sens_pos (device Ns x 3 f64, outside the head) reading the
+ * field along unit orientations sens_dir (device Ns x 3 f64).  The field of
+ * the total current J^p - sigma grad u (Sec. 2.1) by Biot-Savart is the
+ * primary dipole's field plus Bm^T u, with
+ *   Bm[i][s] = -mu0/(4 pi) sum_{e containing i} grad psi_i|_e . sigma_e (G_e(r_s) x n_s),
+ *   G_e(r) = int_e (r - r')/|r - r'|^3 dV' by the 4-point degree-2 rule
+ *   (barycentric points (a, b, b, b), a = (5 + 3 sqrt 5)/20, b = (5 - sqrt 5)/20),
+ * mu0/(4 pi) = 1e-7 T m/A, row i' (the grounding node) zero.  u solves the
+ * system's own A (with whatever electrode terms it was assembled with).
+ * sigma6: device m x 6 f64, the conductivity the system was assembled with. */
+
+/* Bm: device out, n x Ns f64.  Bitwise reproducible (per-node sums in tet
+ * order).  ZI_ERR_NONFINITE if a sensor sits on a quadrature point.
+ * Synchronises. */
+int zi_meg_rhs(zi_system* sys, const double* sigma6, const double* sens_pos, const double* sens_dir, int Ns,
+               double* Bm, cudaStream_t stream);
+
+/* T_meg = A^-1 Bm, one PCG recurrence per sensor (the solver of zi_transfer,
+ * with opts).  T_meg: device out, n x Ns f64; iters (Ns i32) and relres (Ns
+ * f64): host out, may be NULL.  The handle's own T is untouched.
+ * ZI_ERR_NOT_CONVERGED as in zi_transfer.  Synchronises the device. */
+int zi_meg_transfer(zi_system* sys, const double* sigma6, const double* sens_pos, const double* sens_dir, int Ns,
+                    const zi_solver_opts* opts, double* T_meg, int32_t* iters, double* relres,
+                    cudaStream_t stream);
+
+/* MEG lead field of Cartesian sources: L[s][3p + d] = mu0/(4 pi) e_d . ((r_s -
+ * x_p) x n_s) / |r_s - x_p|^3 + (T_meg^T F)[s][3p + d], with F given column by
+ * column (3P x K node indices and loads, 1 <= K <= 32: zi_source_pi or
+ * zi_source_stencil).  pos: device P x 3 f64; T_meg: device n x Ns f64 from
+ * zi_meg_transfer; L: device out, Ns x 3P f64.  ZI_ERR_ARG for a node index
+ * outside the mesh or a non-finite weight.  Synchronises. */
+int zi_meg_leadfield(zi_system* sys, const double* T_meg, const double* sens_pos, const double* sens_dir, int Ns,
+                     const double* pos, int64_t P, const int32_t* F_nodes, const double* F_w, int K, double* L,
+                     cudaStream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Linearised EIT (App. A.3)                                                   */
 /* ------------------------------------------------------------------------ */

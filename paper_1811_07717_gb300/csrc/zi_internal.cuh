@@ -150,6 +150,10 @@ int schur_matrix(zi_system* sys, double* S, cudaStream_t s);  // S = C - B^T T (
 // L = R S^-1 H (CEM) or H (point electrodes) from Ht = (T^T F)^T, N x n_rhs;
 // synchronises the stream.
 int leadfield_finish(zi_system* sys, const double* Ht, int64_t N, double* Lout, cudaStream_t s);
+// Ht[c][l] = sum_j Fw[c*K + j] * T[Fn[c*K + j]][l] for ncols columns (T: n x ncol); bad
+// indices or weights set DEV_ERR_BAD_INDEX in *err (device) and zero that column.
+int source_apply_ell(int64_t ncols, int K, const int32_t* Fn, const double* Fw, int64_t n, const double* T, int ncol,
+                     double* Ht, int* err, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // device helpers

@@ -328,6 +328,13 @@ int leadfield_impl(zi_system* S, const int32_t* dip_tet, int64_t P, double* Lout
   return leadfield_finish(S, Ht.p, 3 * P, Lout, s);
 }
 
+int source_apply_ell(int64_t ncols, int K, const int32_t* Fn, const double* Fw, int64_t n, const double* T, int ncol,
+                     double* Ht, int* err, cudaStream_t s) {
+  k_source_apply_ell<<<grid_for(ncols * 32, 256, 152u * 64u), 256, 0, s>>>(ncols, K, Fn, Fw, n, T, ncol, Ht, err);
+  ZI_LAUNCH_CHECK();
+  return ZI_OK;
+}
+
 int leadfield_sparse_impl(zi_system* S, const int32_t* Fn, const double* Fw, int64_t ncols, int K, double* Lout,
                           cudaStream_t s) {
   const int ncol = S->n_rhs;
@@ -336,9 +343,7 @@ int leadfield_sparse_impl(zi_system* S, const int32_t* Fn, const double* Fw, int
   ZI_CHECK(Ht.alloc((size_t)ncols * ncol, s));
   ZI_CHECK(err.alloc(1, s));
   ZI_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-  k_source_apply_ell<<<grid_for(ncols * 32, 256, 152u * 64u), 256, 0, s>>>(ncols, K, Fn, Fw, S->n, S->T, ncol,
-                                                                          Ht.p, err.p);
-  ZI_LAUNCH_CHECK();
+  ZI_CHECK(source_apply_ell(ncols, K, Fn, Fw, S->n, S->T, ncol, Ht.p, err.p, s));
   ZI_CHECK(read_dev_err(err.p, s));
   return leadfield_finish(S, Ht.p, ncols, Lout, s);
 }

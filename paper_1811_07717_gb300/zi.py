@@ -31,7 +31,8 @@ EXPORTS = ("zi_version", "zi_last_error", "zi_status_string", "zi_mesh_from_grid
            "zi_locate_dipoles_grid", "zi_assemble", "zi_system_set_conductivity",
            "zi_system_get_info", "zi_system_get_matrix", "zi_system_destroy",
            "zi_solver_opts_default", "zi_transfer", "zi_transfer_batched", "zi_leadfield",
-           "zi_source_stencil", "zi_leadfield_sparse", "zi_eit_jacobian", "zi_leadfield_noalloc", "zi_ias_map", "zi_time_spmm", "zi_kernel_launches")
+           "zi_source_stencil", "zi_leadfield_sparse", "zi_source_pi", "zi_meg_rhs",
+           "zi_meg_transfer", "zi_meg_leadfield", "zi_eit_jacobian", "zi_leadfield_noalloc", "zi_ias_map", "zi_time_spmm", "zi_kernel_launches")
 
 
 class ZiError(RuntimeError):
@@ -92,6 +93,10 @@ def load_library(path: str = LIB_PATH):
         "zi_leadfield": ([P, P, I64, ctypes.POINTER(_Opts), P, P], ctypes.c_int),
         "zi_source_stencil": ([P, P, P, I64, ctypes.c_int, D, P, P, P], ctypes.c_int),
         "zi_leadfield_sparse": ([P, P, P, I64, ctypes.c_int, ctypes.POINTER(_Opts), P, P], ctypes.c_int),
+        "zi_source_pi": ([P, P, I64, P, P, P], ctypes.c_int),
+        "zi_meg_rhs": ([P, P, P, P, ctypes.c_int, P, P], ctypes.c_int),
+        "zi_meg_transfer": ([P, P, P, P, ctypes.c_int, ctypes.POINTER(_Opts), P, P, P, P], ctypes.c_int),
+        "zi_meg_leadfield": ([P, P, P, P, ctypes.c_int, P, I64, P, P, ctypes.c_int, P, P], ctypes.c_int),
         "zi_eit_jacobian": ([P, P, ctypes.c_int, ctypes.c_int, P, P, P, ctypes.POINTER(_Opts), P], ctypes.c_int),
         "zi_leadfield_noalloc": ([P, P, I64, P, P], ctypes.c_int),
         "zi_ias_map": ([P, I32, I64, P, I32, D, D, D, I32, I32, P, P, P], ctypes.c_int),
@@ -225,6 +230,7 @@ class System:
         self.nodes = _dev(nodes, torch.float64)
         self.tets = _dev(tets, torch.int32)
         s6 = _dev(sigma6, torch.float64)
+        self.sigma6 = s6  # kept for the MEG volume currents
         self.bfaces = _dev(bfaces, torch.int32)
         self.centres = _dev(centres, torch.float64)
         mdl = ELECTRODE_CEM if model in ("cem", ELECTRODE_CEM) else ELECTRODE_POINT
@@ -269,6 +275,7 @@ class System:
         torch = _torch()
         s6 = _dev(sigma6, torch.float64)
         _check(self._lib.zi_system_set_conductivity(self._h, _ptr(s6), _stream()))
+        self.sigma6 = s6
         self.version += 1
 
     def transfer(self, opts: SolverOpts | None = None, want_T: bool = True, allow_not_converged=False):
@@ -337,6 +344,66 @@ class System:
         the sparse lead field; columns 3p + d as in leadfield()."""
         Fn, Fw = self.source_stencil(pos, dip_tet, model, lam)
         return self.leadfield_sparse(Fn, Fw, opts)
+
+    def source_pi(self, dip_tet):
+        """Partial-integration source columns (zi_source_pi): (F_nodes, F_w), 3P x 4."""
+        torch = _torch()
+        dt = _dev(dip_tet, torch.int32)
+        P = dt.shape[0]
+        Fn = torch.empty((3 * P, 4), dtype=torch.int32, device=self.nodes.device)
+        Fw = torch.empty((3 * P, 4), dtype=torch.float64, device=self.nodes.device)
+        _check(self._lib.zi_source_pi(self._h, _ptr(dt), P, _ptr(Fn), _ptr(Fw), _stream()))
+        return Fn, Fw
+
+    def _sensors(self, sens_pos, sens_dir):
+        torch = _torch()
+        sp_ = _dev(sens_pos, torch.float64).reshape(-1, 3).contiguous()
+        sd = _dev(sens_dir, torch.float64).reshape(-1, 3).contiguous()
+        if sp_.shape != sd.shape:
+            raise ValueError("sensor positions and orientations disagree")
+        return sp_, sd
+
+    def meg_rhs(self, sens_pos, sens_dir):
+        """Bm (n x Ns) of the MEG volume currents (zi_meg_rhs)."""
+        torch = _torch()
+        sp_, sd = self._sensors(sens_pos, sens_dir)
+        Ns = sp_.shape[0]
+        Bm = torch.empty((self.info()["n"], Ns), dtype=torch.float64, device=self.nodes.device)
+        _check(self._lib.zi_meg_rhs(self._h, _ptr(self.sigma6), _ptr(sp_), _ptr(sd), Ns, _ptr(Bm), _stream()))
+        return Bm
+
+    def meg_transfer(self, sens_pos, sens_dir, opts: SolverOpts | None = None, allow_not_converged=False):
+        """T_meg = A^-1 Bm (zi_meg_transfer); returns (T_meg, iters, relres)."""
+        torch = _torch()
+        opts = opts or SolverOpts()
+        sp_, sd = self._sensors(sens_pos, sens_dir)
+        Ns = sp_.shape[0]
+        Tm = torch.empty((self.info()["n"], Ns), dtype=torch.float64, device=self.nodes.device)
+        it = (ctypes.c_int32 * Ns)()
+        rr = (ctypes.c_double * Ns)()
+        o = opts.c()
+        st = self._lib.zi_meg_transfer(self._h, _ptr(self.sigma6), _ptr(sp_), _ptr(sd), Ns, ctypes.byref(o),
+                                       _ptr(Tm), it, rr, _stream())
+        _check(st, allow_not_converged)
+        return Tm, np.array(it[:], dtype=np.int32), np.array(rr[:], dtype=np.float64)
+
+    def meg_leadfield(self, T_meg, sens_pos, sens_dir, pos, F_nodes, F_w):
+        """MEG lead field (zi_meg_leadfield), Ns x 3P, for Cartesian sources at pos
+        with source columns (F_nodes, F_w) from source_pi or source_stencil."""
+        torch = _torch()
+        sp_, sd = self._sensors(sens_pos, sens_dir)
+        ps = _dev(pos, torch.float64).reshape(-1, 3).contiguous()
+        Fn = _dev(F_nodes, torch.int32).contiguous()
+        Fw = _dev(F_w, torch.float64).contiguous()
+        P = ps.shape[0]
+        if Fn.shape != Fw.shape or Fn.dim() != 2 or Fn.shape[0] != 3 * P:
+            raise ValueError("source columns must be 3P x K")
+        Tm = _dev(T_meg, torch.float64).contiguous()
+        Ns = sp_.shape[0]
+        L = torch.empty((Ns, 3 * P), dtype=torch.float64, device=self.nodes.device)
+        _check(self._lib.zi_meg_leadfield(self._h, _ptr(Tm), _ptr(sp_), _ptr(sd), Ns, _ptr(ps), P, _ptr(Fn),
+                                          _ptr(Fw), Fn.shape[1], _ptr(L), _stream()))
+        return L
 
     def eit(self, I, mode=EIT_FULL, grad_y=None, opts: SolverOpts | None = None, want_y=True):
         """Linearised EIT (zi_eit_jacobian): returns (y, out)."""

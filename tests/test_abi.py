@@ -61,6 +61,10 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.zi_ias_map(None, 4, 10, None, 1, 0.1, 1.0, 2.0, 0, 5, None, None, None) == zi.ZI_ERR_ARG
     assert lib.zi_source_stencil(None, None, None, 1, zi.SOURCE_PBO10, 0.0, None, None, None) == zi.ZI_ERR_ARG
     assert lib.zi_leadfield_sparse(None, None, None, 1, 8, None, None, None) == zi.ZI_ERR_ARG
+    assert lib.zi_source_pi(None, None, 1, None, None, None) == zi.ZI_ERR_ARG
+    assert lib.zi_meg_rhs(None, None, None, None, 4, None, None) == zi.ZI_ERR_ARG
+    assert lib.zi_meg_transfer(None, None, None, None, 4, None, None, None, None, None) == zi.ZI_ERR_ARG
+    assert lib.zi_meg_leadfield(None, None, None, None, 4, None, 1, None, None, 4, None, None) == zi.ZI_ERR_ARG
 
 
 def test_default_solver_options(lib):
