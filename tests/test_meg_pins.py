@@ -121,3 +121,22 @@ def test_radial_sensors_see_no_volume_current_in_the_limit():
         Tm = M.meg_transfer(sysm, s6, sp_, sd)
         rel.append(np.linalg.norm(np.asarray((F.T @ Tm).T)) / np.linalg.norm(M.primary(sp_, sd, pos)))
     assert rel[0] > rel[1] > rel[2] and rel[2] < 0.02
+
+
+def test_hdiv_sources_beat_partial_integration_for_meg_too():
+    """The H(div) sources' accuracy (Sec. 2.1) carries over to the magnetic
+    lead field: against Sarvas, PBO10 < Whitney < partial integration."""
+    from oracle import hdiv as HD
+    for h in (0.2, 0.1):
+        mesh, s6, sysm, sp_, sd, pos, q, F = _sphere(h)
+        Tm = M.meg_transfer(sysm, s6, sp_, sd)
+        dip = O.locate_dipoles(mesh, pos)
+        sel = np.nonzero(np.linalg.norm(pos, axis=1) < 0.6)[0]
+        Ba = np.stack([np.sum(analytic.sarvas_field(sp_, pos[p], q[p]) * sd, 1) for p in sel], 1)
+        errs = []
+        for Fm in (F, HD.source_matrix_hdiv(mesh["nodes"], mesh["tets"], dip, pos, HD.WHITNEY4),
+                   HD.source_matrix_hdiv(mesh["nodes"], mesh["tets"], dip, pos, HD.PBO10)):
+            L = M.meg_leadfield(sysm, s6, sp_, sd, pos, Fm, Tm=Tm)
+            Lq = np.stack([L[:, 3 * p:3 * p + 3] @ q[p] for p in sel], 1)
+            errs.append(np.linalg.norm(Lq - Ba) / np.linalg.norm(Ba))
+        assert errs[2] < errs[1] < errs[0]
