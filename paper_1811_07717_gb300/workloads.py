@@ -211,3 +211,38 @@ def meg_sensors(n: int, radius: float, tilt: float = 0.6):
     d = rhat + tilt * t
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     return np.ascontiguousarray(pos), np.ascontiguousarray(d)
+
+
+def icosphere(level: int, radius: float = 1.0, centre=(0.0, 0.0, 0.0)):
+    """Closed triangle surface of a sphere: the icosahedron with every
+    triangle split into four `level` times, vertices projected to the sphere;
+    triangles oriented outward.  Returns (verts (v,3), tris (t,3) int32)."""
+    p = (1.0 + math.sqrt(5.0)) / 2.0
+    v = [(-1, p, 0), (1, p, 0), (-1, -p, 0), (1, -p, 0), (0, -1, p), (0, 1, p), (0, -1, -p), (0, 1, -p),
+         (p, 0, -1), (p, 0, 1), (-p, 0, -1), (-p, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+         (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11),
+         (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    verts = [np.array(x, dtype=np.float64) / np.linalg.norm(x) for x in v]
+    for _ in range(level):
+        mid = {}
+
+        def midpoint(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in mid:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                mid[key] = len(verts) - 1
+            return mid[key]
+        nf = []
+        for a, b, c in f:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        f = nf
+    V = np.array(verts) * radius + np.asarray(centre, dtype=np.float64)
+    T = np.array(f, dtype=np.int32)
+    # outward orientation: the normal points away from the centre
+    n = np.cross(V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]])
+    flip = np.einsum("ij,ij->i", n, V[T].mean(axis=1) - np.asarray(centre)) < 0
+    T[flip, 1], T[flip, 2] = T[flip, 2].copy(), T[flip, 1].copy()
+    return V, T
