@@ -153,3 +153,38 @@ def test_compartment_volumes_converge():
             assert mesh["labels"][t] == S.tet_label(glab[gidx[t]], (1, 2, 3))
     assert np.all(err[1] < 0.25)
     assert err[1][0] < 0.7 * err[0][0] and np.abs(err[1]).sum() < np.abs(err[0]).sum()
+
+
+def _locate_brute_force(nodes, tets, pos):
+    """The tet whose smallest barycentric coordinate at the point is largest."""
+    M = np.ones((tets.shape[0], 4, 4))
+    M[:, :, 1:] = nodes[tets]
+    inv = np.linalg.inv(M)
+    out = np.empty(pos.shape[0], dtype=np.int64)
+    for p, x in enumerate(pos):
+        lam = np.einsum("mji,j->mi", inv, np.concatenate([[1.0], x]))
+        out[p] = np.argmax(lam.min(axis=1))
+    return out
+
+
+def test_lead_field_on_a_segmentation_mesh_converges_to_the_analytic_ball():
+    """End to end: the mesh of one icosphere surface feeds the EEG build, and
+    its lead field approaches the homogeneous-ball potential as h falls."""
+    from oracle import analytic
+    errs = []
+    for h in (0.2, 0.1):
+        spec = W.unit_sphere_point(h=h, n_electrodes=16, n_dipoles=40)
+        mesh = S.mesh_from_surfaces(h, [W.icosphere(3, 1.0)], (1,))
+        s6 = W.conductivity(spec, mesh["nodes"], mesh["tets"], mesh["labels"])
+        centres, _ = W.electrode_inputs(spec)
+        pos, q = W.dipole_inputs(spec)
+        sysm = O.System(mesh, s6, centres, "point")
+        dip = _locate_brute_force(mesh["nodes"], mesh["tets"], pos)
+        L = O.leadfield(sysm, O.source_matrix(sysm.n, mesh["nodes"], mesh["tets"], dip))
+        sel = np.nonzero(np.linalg.norm(pos, axis=1) < 0.6)[0]
+        Lq = np.stack([L[:, 3 * p:3 * p + 3] @ q[p] for p in sel], 1)
+        ua = np.stack([analytic.sphere_dipole_potential(mesh["nodes"][sysm.el_nodes], pos[p], q[p], 0.33, 1.0)
+                       for p in sel], 1)
+        ua = ua[1:] - ua[0]
+        errs.append(np.linalg.norm(Lq - ua) / np.linalg.norm(ua))
+    assert errs[1] < 0.6 * errs[0] and errs[1] < 0.2
