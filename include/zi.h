@@ -114,6 +114,34 @@ int zi_mesh_from_grid(double h, int n_shells, const double* radii,
                       double* nodes, int32_t* tets, int32_t* labels, int32_t* bfaces,
                       cudaStream_t stream);
 
+/* Mesh from a surface segmentation (Sec. 2.5, mesh tool): the Kuhn grid of
+ * zi_mesh_from_grid over [-N h, N h]^3, N = ceil(max |vertex coordinate| / h) + 1,
+ * labelled from closed, outward-oriented triangle surfaces, one per
+ * compartment, innermost first.
+ *   node label: the first surface whose winding number at the node is >= 1/2
+ *     (the sum of its triangles' solid angles over 4 pi, Van Oosterom-Strackee);
+ *   tet label: among its four node labels, the compartment with the lowest
+ *     priority value (ties to the inner compartment); a tet with no node
+ *     inside any surface is dropped;
+ *   nodes (vertices of kept tets) in grid order, tets in (cube, permutation)
+ *   order, positively oriented; bfaces: faces of exactly one kept tet, in
+ *   (tet, local face) order, outward.
+ *   tri_offset: host, n_surf + 1 i64, triangles of surface c are
+ *     tri_offset[c] .. tri_offset[c+1] - 1 (tri_offset[0] = 0, each non-empty);
+ *   priority: host, n_surf i32; verts: device nv x 3 f64; tris: device nt x 3
+ *     i32 indices into verts.  1 <= n_surf <= 64, N <= 301.
+ * Two calls: first with the four outputs NULL to get the counts, then with
+ * all four allocated from them and *n_nodes, *n_tets, *n_bfaces still holding
+ * those counts (the call checks them before writing).  ZI_ERR_NONFINITE for a
+ * non-finite vertex, ZI_ERR_ARG for a triangle index outside verts.  A node
+ * lying on a surface gets the winding number's rounding (about 1/2): keep
+ * surfaces off the grid nodes where labels must be exact.  Synchronises. */
+int zi_mesh_from_surfaces(double h, int n_surf, const int64_t* tri_offset, const int32_t* priority,
+                          const double* verts, int64_t nv, const int32_t* tris,
+                          int64_t* n_nodes, int64_t* n_tets, int64_t* n_bfaces,
+                          double* nodes, int32_t* tets, int32_t* labels, int32_t* bfaces,
+                          cudaStream_t stream);
+
 /* Element of a zi_mesh_from_grid mesh (same h, radii) that holds each point:
  * cube = floor(x/h) per axis, then the Kuhn tet whose axis order sorts the
  * fractional coordinates in descending order (first permutation on ties).

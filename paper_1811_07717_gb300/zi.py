@@ -28,7 +28,7 @@ STENCIL_WIDTH = 8
 
 # Every symbol include/zi.h declares.
 EXPORTS = ("zi_version", "zi_last_error", "zi_status_string", "zi_mesh_from_grid",
-           "zi_locate_dipoles_grid", "zi_assemble", "zi_system_set_conductivity",
+           "zi_locate_dipoles_grid", "zi_mesh_from_surfaces", "zi_assemble", "zi_system_set_conductivity",
            "zi_system_get_info", "zi_system_get_matrix", "zi_system_destroy",
            "zi_solver_opts_default", "zi_transfer", "zi_transfer_batched", "zi_leadfield",
            "zi_source_stencil", "zi_leadfield_sparse", "zi_source_pi", "zi_meg_rhs",
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
         "zi_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "zi_mesh_from_grid": ([D, ctypes.c_int, P, P, P, P, P, P, P, P, P], ctypes.c_int),
         "zi_locate_dipoles_grid": ([D, ctypes.c_int, P, P, I64, P, P], ctypes.c_int),
+        "zi_mesh_from_surfaces": ([D, ctypes.c_int, P, P, P, I64, P, P, P, P, P, P, P, P, P], ctypes.c_int),
         "zi_assemble": ([P, I64, P, I64, P, P, I64, ctypes.POINTER(_Electrodes), P, P], ctypes.c_int),
         "zi_system_set_conductivity": ([P, P, P], ctypes.c_int),
         "zi_system_get_info": ([P, ctypes.POINTER(_Info)], ctypes.c_int),
@@ -207,6 +208,41 @@ def mesh_from_grid(h: float, radii, device="cuda"):
     _check(lib.zi_mesh_from_grid(h, len(radii), rb, ctypes.byref(n), ctypes.byref(m), ctypes.byref(nb),
                                  _ptr(nodes), _ptr(tets), _ptr(labels), _ptr(bfaces), st))
     return dict(nodes=nodes, tets=tets, labels=labels, bfaces=bfaces, h=float(h), radii=tuple(radii))
+
+
+def mesh_from_surfaces(h: float, surfaces, priority, device="cuda"):
+    """Mesh of a surface segmentation (zi_mesh_from_surfaces): surfaces is a
+    list of (verts (v,3), tris (t,3)) closed outward-oriented surfaces,
+    innermost first; priority one int per surface (lower wins).  Returns a
+    dict of CUDA tensors like mesh_from_grid."""
+    torch = _torch()
+    lib = load_library()
+    if len(priority) != len(surfaces):
+        raise ValueError("one priority per surface")
+    vs, ts, off, base = [], [], [0], 0
+    for v, t in surfaces:
+        v = np.asarray(v, dtype=np.float64).reshape(-1, 3)
+        t = np.asarray(t, dtype=np.int64).reshape(-1, 3)
+        vs.append(v)
+        ts.append(t + base)
+        base += v.shape[0]
+        off.append(off[-1] + t.shape[0])
+    verts = _dev(np.concatenate(vs), torch.float64, device)
+    tris = _dev(np.concatenate(ts).astype(np.int32), torch.int32, device)
+    toff = (ctypes.c_int64 * len(off))(*off)
+    pr = (ctypes.c_int32 * len(priority))(*[int(x) for x in priority])
+    n, m, nb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    st = _stream()
+    args = (float(h), len(surfaces), toff, pr, _ptr(verts), verts.shape[0], _ptr(tris))
+    _check(lib.zi_mesh_from_surfaces(*args, ctypes.byref(n), ctypes.byref(m), ctypes.byref(nb),
+                                     None, None, None, None, st))
+    nodes = torch.empty((n.value, 3), dtype=torch.float64, device=device)
+    tets = torch.empty((m.value, 4), dtype=torch.int32, device=device)
+    labels = torch.empty((m.value,), dtype=torch.int32, device=device)
+    bfaces = torch.empty((nb.value, 3), dtype=torch.int32, device=device)
+    _check(lib.zi_mesh_from_surfaces(*args, ctypes.byref(n), ctypes.byref(m), ctypes.byref(nb),
+                                     _ptr(nodes), _ptr(tets), _ptr(labels), _ptr(bfaces), st))
+    return dict(nodes=nodes, tets=tets, labels=labels, bfaces=bfaces, h=float(h))
 
 
 def locate_dipoles_grid(h: float, radii, pos):

@@ -1,0 +1,85 @@
+"""GPU parity of the segmentation mesher (Sec. 2.5, mesh tool) through the C
+ABI: nodes, tets, labels and boundary faces bit-exact against the oracle on
+surfaces kept off the grid nodes (so every label is decided far from the
+winding number's threshold), the lead field of the GPU mesh against the
+oracle's, and the error paths the kernels check."""
+import numpy as np
+import pytest
+
+from oracle import segmesh as S, zi_oracle as O
+from paper_1811_07717_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1811_07717_gb300 import zi  # noqa: E402
+
+CENTRE = (0.013, -0.007, 0.011)
+
+
+def clear_of_threshold(h, surfaces):
+    """Every grid node's winding number is far from 1/2 for every surface."""
+    R = max(float(np.max(np.abs(v))) for v, _ in surfaces)
+    N = int(np.ceil(R / h)) + 1
+    ax = (np.arange(2 * N + 1) - N) * h
+    P = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3)
+    return all(np.min(np.abs(S.winding_number(P, v, t) - 0.5)) > 1e-6 for v, t in surfaces)
+
+
+CASES = [
+    (0.2, [W.icosphere(2, r, CENTRE) for r in (0.8, 0.86, 1.0)], (3, 1, 2)),
+    (0.2, [W.icosphere(2, r, CENTRE) for r in (0.8, 0.86, 1.0)], (1, 2, 3)),
+    (0.15, [W.icosphere(3, 0.97, CENTRE)], (1,)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_mesh_from_surfaces_bit_exact(case):
+    h, surf, prio = CASES[case]
+    assert clear_of_threshold(h, surf)
+    ref = S.mesh_from_surfaces(h, surf, prio)
+    got = zi.mesh_from_surfaces(h, surf, prio)
+    assert np.array_equal(got["nodes"].cpu().numpy(), ref["nodes"])
+    assert np.array_equal(got["tets"].cpu().numpy(), ref["tets"])
+    assert np.array_equal(got["labels"].cpu().numpy(), ref["labels"])
+    assert np.array_equal(got["bfaces"].cpu().numpy(), ref["bfaces"])
+
+
+def test_lead_field_on_the_gpu_mesh_matches_the_oracle():
+    h, surf, prio = CASES[2]
+    ref = S.mesh_from_surfaces(h, surf, prio)
+    got = zi.mesh_from_surfaces(h, surf, prio)
+    spec = W.unit_sphere_point(h=h, n_electrodes=16, n_dipoles=30)
+    s6 = W.conductivity(spec, ref["nodes"], ref["tets"], ref["labels"])
+    centres, _ = W.electrode_inputs(spec)
+    pos, _ = W.dipole_inputs(spec)
+    # the tet holding each dipole: largest smallest barycentric coordinate
+    M = np.ones((ref["tets"].shape[0], 4, 4))
+    M[:, :, 1:] = ref["nodes"][ref["tets"]]
+    inv = np.linalg.inv(M)
+    dip = np.array([np.argmax(np.einsum("mji,j->mi", inv, np.concatenate([[1.0], x])).min(axis=1)) for x in pos])
+    osys = O.System(ref, s6, centres, "point")
+    Lo = O.leadfield(osys, O.source_matrix(osys.n, ref["nodes"], ref["tets"], dip))
+    gsys = zi.System(got["nodes"], got["tets"], s6, got["bfaces"], centres, model="point")
+    Lg = gsys.leadfield(torch.from_numpy(dip.astype(np.int32)), zi.SolverOpts(tol=1e-12)).cpu().numpy()
+    assert np.linalg.norm(Lg - Lo) <= 1e-8 * np.linalg.norm(Lo)
+    gsys.close()
+
+
+def test_mesh_from_surfaces_errors():
+    V, T = W.icosphere(1, 0.9, CENTRE)
+    bad = T.copy()
+    bad[3, 1] = V.shape[0]
+    with pytest.raises(zi.ZiError) as e:
+        zi.mesh_from_surfaces(0.3, [(V, bad)], (1,))
+    assert e.value.status == zi.ZI_ERR_ARG
+    Vn = V.copy()
+    Vn[2, 0] = np.nan
+    with pytest.raises(zi.ZiError) as e:
+        zi.mesh_from_surfaces(0.3, [(Vn, T)], (1,))
+    assert e.value.status == zi.ZI_ERR_NONFINITE
+    with pytest.raises(ValueError):
+        zi.mesh_from_surfaces(0.3, [(V, T)], (1, 2))
