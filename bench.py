@@ -39,7 +39,7 @@ WORKLOAD = "three-shell sphere 80/86/92 mm, h=2 mm Kuhn grid (428185 nodes, 2447
            "128 CEM electrodes r=5 mm z=2e-3 Ohm m^2, 20000 dipoles x 3, PCG tol 1e-10"
 # ncu DRAM traffic per launch of the FP32 SpMM on this workload, from the capture
 # summarised in profiles/ (None until taken, or once the kernel source changed).
-SPMM_TRAFFIC = {"source_sha": "46c2569dbf4e86ad", "bytes": 246.94656e6 + 184.47488e6}
+SPMM_TRAFFIC = {"source_sha": "8e30f73bd16fd9df", "bytes": 246.94656e6 + 184.47488e6}
 
 
 def parse():

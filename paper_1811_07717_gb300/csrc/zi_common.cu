@@ -94,7 +94,7 @@ static int get_pool(cudaMemPool_t* out) {
 }
 
 int dalloc(void** p, size_t bytes, cudaStream_t s) {
-  cudaMemPool_t pool;
+  cudaMemPool_t pool = nullptr;
   ZI_CHECK(get_pool(&pool));
   cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
   if (e != cudaSuccess) {

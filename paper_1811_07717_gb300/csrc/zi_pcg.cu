@@ -1548,8 +1548,8 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
 __global__ void __launch_bounds__(FIN_THREADS) k_init_cols(int nblk, int ld, int ncol,
                                                            const double* __restrict__ part_rr,
                                                            const double* __restrict__ bb, double tol2,
-                                                           const int* __restrict__ skip, double* __restrict__ rho,
-                                                           double* __restrict__ stop2, int* __restrict__ conv,
+                                                           const int* skip, double* __restrict__ rho,
+                                                           double* __restrict__ stop2, int* conv,  // may alias skip
                                                            int* __restrict__ iters, int* __restrict__ cnt) {
   __shared__ double sm[FIN_THREADS];
   __shared__ int nact;
