@@ -98,6 +98,41 @@ def oracle_once() -> float:
     return float(r.stdout.strip().splitlines()[-1])
 
 
+HDIV_SAMPLE_TEXT = ("oracle LF build with PBO 10-source H(div) sources (numpy stencils and KKT solves + SuperLU "
+                    "direct solve, 1 thread) of the three-shell head, 128 CEM electrodes and 20000 sources at h=4 mm")
+MEG_SAMPLE_TEXT = ("oracle MEG LF build (numpy right-hand sides + SuperLU direct solve, 1 thread) of the three-shell "
+                   "head at h=4 mm, 32 of the 256 magnetometers, 20000 partial-integration dipoles")
+
+
+def oracle_sample_once(kind: str) -> float:
+    """One oracle build of the H(div) ("hdiv") or MEG ("meg") sample at h = 4 mm,
+    in a fresh single-threaded process."""
+    body = {
+        "hdiv": ("mesh, s6, c, z, pos, q = O.build_head(spec, W)\n"
+                 "S = O.System(mesh, s6, c, spec.electrode_model, radius=spec.electrode_radius, z=z)\n"
+                 "dip = O.locate_dipoles(mesh, pos)\n"
+                 "F = HD.source_matrix_hdiv(mesh['nodes'], mesh['tets'], dip, pos, HD.PBO10)\n"
+                 "L = O.leadfield(S, F)\n"),
+        "meg": ("mesh, s6, c, z, pos, q = O.build_head(spec, W)\n"
+                "S = O.System(mesh, s6, c, spec.electrode_model, radius=spec.electrode_radius, z=z)\n"
+                "sp_, sd = W.meg_sensors(256, spec.radii[-1] + 0.02)\n"
+                "dip = O.locate_dipoles(mesh, pos)\n"
+                "F = O.source_matrix(S.n, mesh['nodes'], mesh['tets'], dip)\n"
+                "L = M.meg_leadfield(S, s6, sp_[:32], sd[:32], pos, F)\n"),
+    }[kind]
+    code = ("import sys,time; sys.path.insert(0, %r)\n"
+            "from oracle import zi_oracle as O, hdiv as HD, meg as M\n"
+            "from paper_1811_07717_gb300 import workloads as W\n"
+            "spec = W.three_shell(%r, %d, %d, seed=2)\n"
+            "t = time.perf_counter()\n%sprint(time.perf_counter() - t)\n"
+            % (ROOT, ORACLE_SAMPLE["h"], ORACLE_SAMPLE["electrodes"], ORACLE_SAMPLE["dipoles"], body))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-500:])
+    return float(r.stdout.strip().splitlines()[-1])
+
+
 def cpu_pcg_once() -> dict:
     """The CPU block PCG baseline (oracle/cpu_pcg.c: the same Jacobi PCG,
     FP64, OpenMP over all host cores) on the oracle sample's matrix, in a
@@ -430,6 +465,17 @@ def eit_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def cpu_leg(kind, text, args):
+    """cpu_baseline of the H(div) and MEG lines (rank 0 at N=1 only; skipped
+    by --no-cpu); a failure is reported, never replaced."""
+    if args.no_cpu or dist_env()[1] != 1:
+        return None
+    try:
+        return {"value": oracle_sample_once(kind), "unit": "s", "cores": 1, "kind": "oracle", "sample": text}
+    except Exception as ex:
+        return {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": "failed: %s" % ex}
+
+
 def hdiv_workload(args):
     """The 2 mm lead-field build with Cartesian H(div) sources (PBO 10-source
     stencil, Sec. 2.1) in place of partial integration: the whole build, and
@@ -491,6 +537,7 @@ def hdiv_workload(args):
             "data": "synthetic",
             "config": {"workload": "three-shell 2 mm head (428185 nodes, 2447424 tets), 128 CEM electrodes, "
                                    "20000 H(div) sources x 3 orientations, PCG tol 1e-10, mixed precision"},
+            "cpu_baseline": cpu_leg("hdiv", HDIV_SAMPLE_TEXT, args),
             "source_stencil_s": t_stencil, "leadfield_sparse_s": t_sparse,
             "leadfield_partial_integration_s": t_pi,
             "gpu_launches": int(launches), "clocks": clk.summary()}
@@ -561,6 +608,7 @@ def meg_workload(args):
             "config": {"workload": "three-shell 2 mm head (428185 nodes, 2447424 tets), 128 CEM electrodes "
                                    "attached, 256 magnetometers on a 112 mm sphere (radial + 0.6 tangential), "
                                    "20000 dipoles x 3, PCG tol 1e-10, mixed precision"},
+            "cpu_baseline": cpu_leg("meg", MEG_SAMPLE_TEXT, args),
             "meg_rhs_s": t_rhs, "iterations_max": int(it.max()), "relres_max": float(rr.max()),
             "roofline": {"bound": "alu", "kernel": "k_meg_tet (FP64 kernel integrals per tet and sensor)",
                          "achieved": flops / t_rhs / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
