@@ -3,7 +3,7 @@ solver's work vectors and scaled matrices exist, then launches the solver's
 SpMM on its own (zi_time_spmm) so an ncu capture can select it:
 
     ncu --set full --clock-control none -k regex:k_spmm_dot -s 1 -c 1 \\
-        -o gpurun_out/prof python -m paper_1811_07717_gb300.prof --h 0.002 --precision mixed
+        -o prof python -m paper_1811_07717_gb300.prof --h 0.002 --precision mixed
 
 The first k_spmm_dot launch belongs to the one-iteration transfer; the
 second is the standalone one.  Prints the CUDA-event time of the standalone
