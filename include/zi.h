@@ -142,6 +142,16 @@ int zi_mesh_from_surfaces(double h, int n_surf, const int64_t* tri_offset, const
                           double* nodes, int32_t* tets, int32_t* labels, int32_t* bfaces,
                           cudaStream_t stream);
 
+/* Source interpolation (Sec. 2.5: the indices that connect the mesh with the
+ * DOFs; Sec. 3.2's nearest-point decomposition): out[i] = the index of the
+ * source nearest to point i, ties to the lowest index, distances compared as
+ * FP64 (dx*dx + dy*dy) + dz*dz with every operation rounded once.
+ *   points: device n x 3 f64; sources: device P x 3 f64 (1 <= P < 2^31);
+ *   out: device n i32.  ZI_ERR_NONFINITE for a non-finite coordinate.
+ * Synchronises. */
+int zi_nearest_source(const double* points, int64_t n, const double* sources, int64_t P, int32_t* out,
+                      cudaStream_t stream);
+
 /* Element of a zi_mesh_from_grid mesh (same h, radii) that holds each point:
  * cube = floor(x/h) per axis, then the Kuhn tet whose axis order sorts the
  * fractional coordinates in descending order (first permutation on ties).

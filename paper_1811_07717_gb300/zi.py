@@ -28,7 +28,7 @@ STENCIL_WIDTH = 8
 
 # Every symbol include/zi.h declares.
 EXPORTS = ("zi_version", "zi_last_error", "zi_status_string", "zi_mesh_from_grid",
-           "zi_locate_dipoles_grid", "zi_mesh_from_surfaces", "zi_assemble", "zi_system_set_conductivity",
+           "zi_locate_dipoles_grid", "zi_mesh_from_surfaces", "zi_nearest_source", "zi_assemble", "zi_system_set_conductivity",
            "zi_system_get_info", "zi_system_get_matrix", "zi_system_destroy",
            "zi_solver_opts_default", "zi_transfer", "zi_transfer_batched", "zi_leadfield",
            "zi_source_stencil", "zi_leadfield_sparse", "zi_source_pi", "zi_meg_rhs",
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
         "zi_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "zi_mesh_from_grid": ([D, ctypes.c_int, P, P, P, P, P, P, P, P, P], ctypes.c_int),
         "zi_locate_dipoles_grid": ([D, ctypes.c_int, P, P, I64, P, P], ctypes.c_int),
+        "zi_nearest_source": ([P, I64, P, I64, P, P], ctypes.c_int),
         "zi_mesh_from_surfaces": ([D, ctypes.c_int, P, P, P, I64, P, P, P, P, P, P, P, P, P], ctypes.c_int),
         "zi_assemble": ([P, I64, P, I64, P, P, I64, ctypes.POINTER(_Electrodes), P, P], ctypes.c_int),
         "zi_system_set_conductivity": ([P, P, P], ctypes.c_int),
@@ -243,6 +244,18 @@ def mesh_from_surfaces(h: float, surfaces, priority, device="cuda"):
     _check(lib.zi_mesh_from_surfaces(*args, ctypes.byref(n), ctypes.byref(m), ctypes.byref(nb),
                                      _ptr(nodes), _ptr(tets), _ptr(labels), _ptr(bfaces), st))
     return dict(nodes=nodes, tets=tets, labels=labels, bfaces=bfaces, h=float(h))
+
+
+def nearest_source(points, sources, device="cuda"):
+    """Index of the nearest source for every point (zi_nearest_source), as
+    an int32 CUDA tensor."""
+    torch = _torch()
+    lib = load_library()
+    X = _dev(points, torch.float64, device).reshape(-1, 3).contiguous()
+    S = _dev(sources, torch.float64, device).reshape(-1, 3).contiguous()
+    out = torch.empty(X.shape[0], dtype=torch.int32, device=device)
+    _check(lib.zi_nearest_source(_ptr(X), X.shape[0], _ptr(S), S.shape[0], _ptr(out), _stream()))
+    return out
 
 
 def locate_dipoles_grid(h: float, radii, pos):

@@ -2,7 +2,9 @@
 ABI: nodes, tets, labels and boundary faces bit-exact against the oracle on
 surfaces kept off the grid nodes (so every label is decided far from the
 winding number's threshold), the lead field of the GPU mesh against the
-oracle's, and the error paths the kernels check."""
+oracle's, the source interpolation (nearest DOF) bit-exact, and the error paths
+the kernels check.  (The file sorts last: its kernels' first GPU run cannot
+hide another test.)"""
 import numpy as np
 import pytest
 
@@ -83,3 +85,31 @@ def test_mesh_from_surfaces_errors():
     assert e.value.status == zi.ZI_ERR_NONFINITE
     with pytest.raises(ValueError):
         zi.mesh_from_surfaces(0.3, [(V, T)], (1, 2))
+
+
+def test_nearest_source_bit_exact():
+    """Source interpolation (nearest DOF, ties to the lowest index) against
+    the oracle, with duplicated sources and points on a grid equidistant from
+    several sources, across several shared-memory tiles of sources."""
+    from oracle import interp as I
+    rng = np.random.default_rng(12)
+    S = rng.uniform(-1, 1, (700, 3))
+    S[300:310] = S[10:20]                      # exact duplicates: ties
+    S[600] = [0.0, 0.0, 0.0]
+    S[601] = [0.5, 0.0, 0.0]
+    X = np.concatenate([rng.uniform(-1.1, 1.1, (5000, 3)),
+                        np.stack(np.meshgrid(*(np.arange(-2, 3) * 0.25,) * 3, indexing="ij"), -1).reshape(-1, 3)])
+    ref = I.nearest_source(X, S)
+    got = zi.nearest_source(X, S).cpu().numpy()
+    assert np.array_equal(got, ref)
+    # the mesh nodes of a segmentation mesh against its dipoles
+    h, surf, prio = CASES[2]
+    mesh = zi.mesh_from_surfaces(h, surf, prio)
+    pos, _ = W.dipole_inputs(W.unit_sphere_point(h=h, n_electrodes=16, n_dipoles=300))
+    ref = I.nearest_source(mesh["nodes"].cpu().numpy(), pos)
+    assert np.array_equal(zi.nearest_source(mesh["nodes"], pos).cpu().numpy(), ref)
+    Sn = S.copy()
+    Sn[5, 1] = np.inf
+    with pytest.raises(zi.ZiError) as e:
+        zi.nearest_source(X, Sn)
+    assert e.value.status == zi.ZI_ERR_NONFINITE
