@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison build")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="shell2mm", choices=["shell2mm", "aniso1mm", "batch", "ias", "eit", "hdiv", "meg"],
+    ap.add_argument("--workload", default="shell2mm", choices=["shell2mm", "aniso1mm", "batch", "ias", "eit", "hdiv", "meg", "segmesh"],
                     help="shell2mm: the headline workload; aniso1mm: 1 mm anisotropic-skull head, 256 "
                          "electrodes, 100k dipoles; batch: 24 heads, batched vs per-head solves")
     return ap.parse_args()
@@ -618,6 +618,49 @@ def meg_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def segmesh_workload(args):
+    """The mesher from a surface segmentation (Sec. 2.5) on three nested
+    icosphere surfaces (80 / 86 / 92 mm, 5120 triangles each) at h = 2 mm,
+    skull first by priority, then the nearest-DOF interpolation of the mesh
+    nodes to 20,000 source positions."""
+    import torch
+    from paper_1811_07717_gb300 import workloads as W
+    from paper_1811_07717_gb300 import _build, zi
+    _build.build()
+    centre = (0.00013, -0.00007, 0.00011)  # keeps the surfaces off the grid nodes
+    surf = [W.icosphere(4, r, centre) for r in (0.080, 0.086, 0.092)]
+    prio = (2, 1, 3)
+    pos = torch.from_numpy(W.random_dipoles(20000, 0.078, 2)[0]).cuda()
+
+    def ev_time(fn, reps):
+        fn()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record()
+        for _ in range(reps):
+            out = fn()
+        t1.record()
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3 / reps, out
+
+    with Clocks(torch.cuda.current_device()) as clk:
+        t_mesh, mesh = ev_time(lambda: zi.mesh_from_surfaces(0.002, surf, prio), max(1, args.steps))
+        t_interp, _ = ev_time(lambda: zi.nearest_source(mesh["nodes"], pos), max(1, args.steps))
+    G = 2 * (int(np.ceil(0.0921 / 0.002)) + 1) + 1
+    n_tri = sum(t.shape[0] for _, t in surf)
+    line = {"metric": "segmentation mesh s (3 surfaces, h = 2 mm)", "value": t_mesh, "unit": "s", "n_gpus": 1,
+            "steps": args.steps, "warmup": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "three nested icospheres 80/86/92 mm (5120 triangles each), h = 2 mm grid, "
+                                   "priorities skull > brain > scalp; nearest of 20000 source positions per node",
+                       "grid_nodes": G ** 3, "triangles": n_tri, "mesh_nodes": int(mesh["nodes"].shape[0]),
+                       "mesh_tets": int(mesh["tets"].shape[0])},
+            "interpolation_s": t_interp,
+            "note": "winding numbers by brute force: grid nodes x triangles solid angles (two passes, counts "
+                    "then outputs)",
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -650,6 +693,8 @@ def main():
         return hdiv_workload(args)
     if args.workload == "meg":
         return meg_workload(args)
+    if args.workload == "segmesh":
+        return segmesh_workload(args)
     spec = W.config_three_shell_2mm() if args.workload == "shell2mm" else W.config_three_shell_1mm_aniso()
     workload = WORKLOAD if args.workload == "shell2mm" else (
         "three-shell sphere 80/86/92 mm, h=1 mm Kuhn grid (3342701 nodes, 19573872 tets), transversely "
