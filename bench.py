@@ -683,6 +683,11 @@ def main():
     from paper_1811_07717_gb300 import _build, zi
     _build.build()
 
+    if args.workload not in ("shell2mm", "aniso1mm") and world > 1:
+        # the single-GPU workloads (batch, IAS, EIT, H(div), MEG, mesher) run on rank 0 alone
+        if rank != 0:
+            dist.destroy_process_group()
+            return
     if args.workload == "batch":
         return batch_workload(args)
     if args.workload == "ias":
