@@ -140,3 +140,15 @@ def test_hdiv_sources_beat_partial_integration_for_meg_too():
             Lq = np.stack([L[:, 3 * p:3 * p + 3] @ q[p] for p in sel], 1)
             errs.append(np.linalg.norm(Lq - Ba) / np.linalg.norm(Ba))
         assert errs[2] < errs[1] < errs[0]
+
+
+def test_meg_lead_field_is_blind_to_a_global_conductivity_scale():
+    """Scaling every conductivity by a scales A and Bm alike, so T_meg and the
+    MEG lead field do not change (the EEG lead field scales by 1/a)."""
+    mesh, s6, sysm, sp_, sd, pos, q, F = _sphere(0.2)
+    L1 = M.meg_leadfield(sysm, s6, sp_, sd, pos, F)
+    centres = W.electrode_inputs(W.unit_sphere_point(h=0.2, n_electrodes=16, n_dipoles=40))[0]
+    sys3 = O.System(mesh, 3.0 * s6, centres, "point")
+    L3 = M.meg_leadfield(sys3, 3.0 * s6, sp_, sd, pos, F)
+    assert np.linalg.norm(L3 - L1) <= 1e-11 * np.linalg.norm(L1)
+    assert np.linalg.norm(O.leadfield(sys3, F) * 3.0 - O.leadfield(sysm, F)) <= 1e-11 * np.linalg.norm(O.leadfield(sysm, F))
