@@ -2,7 +2,8 @@
 ABI: nodes, tets, labels and boundary faces bit-exact against the oracle on
 surfaces kept off the grid nodes (so every label is decided far from the
 winding number's threshold), the lead field of the GPU mesh against the
-oracle's, the source interpolation (nearest DOF) bit-exact, and the error paths
+oracle's, the source interpolation (nearest DOF) bit-exact, empty inputs of the
+source and sensor calls, and the error paths
 the kernels check.  (The file sorts last: its kernels' first GPU run cannot
 hide another test.)"""
 import numpy as np
@@ -113,3 +114,27 @@ def test_nearest_source_bit_exact():
     with pytest.raises(zi.ZiError) as e:
         zi.nearest_source(X, Sn)
     assert e.value.status == zi.ZI_ERR_NONFINITE
+
+
+def test_empty_inputs_of_the_source_and_sensor_calls():
+    """Zero sources, columns or points: the calls return empty results
+    without launching work on empty arrays."""
+    spec = W.unit_sphere_point(h=0.2, n_electrodes=8, n_dipoles=5)
+    mesh = zi.mesh_from_grid(spec.h, spec.radii)
+    s6 = W.conductivity(spec, *(mesh[k].cpu().numpy() for k in ("nodes", "tets", "labels")))
+    centres, _ = W.electrode_inputs(spec)
+    system = zi.System(mesh["nodes"], mesh["tets"], s6, mesh["bfaces"], centres, model="point")
+    opts = zi.SolverOpts(tol=1e-10)
+    no_pos = np.zeros((0, 3))
+    no_tet = np.zeros(0, dtype=np.int32)
+    Fn, Fw = system.source_stencil(no_pos, no_tet)
+    assert Fn.shape == (0, zi.STENCIL_WIDTH) and Fw.shape == (0, zi.STENCIL_WIDTH)
+    L = system.leadfield_sparse(np.zeros((0, 4), dtype=np.int32), np.zeros((0, 4)), opts)
+    assert L.shape == (spec.n_electrodes - 1, 0)
+    Fn, Fw = system.source_pi(no_tet)
+    assert Fn.shape == (0, 4)
+    sp_, sd = W.meg_sensors(4, 1.2)
+    Tm, _, _ = system.meg_transfer(sp_, sd, opts)
+    assert system.meg_leadfield(Tm, sp_, sd, no_pos, Fn, Fw).shape == (4, 0)
+    assert zi.nearest_source(no_pos, np.ones((3, 3))).shape == (0,)
+    system.close()
