@@ -601,3 +601,28 @@ def test_difference_form_operator_is_the_matrix():
     err_diff = np.abs(diff - ex)
     assert np.linalg.norm(err_diff) < 0.2 * np.linalg.norm(err_plain)
     assert np.linalg.norm(err_diff[interior]) < 0.02 * np.linalg.norm(err_plain[interior])
+
+
+def test_point_electrodes_are_the_nearest_boundary_nodes():
+    """Electrode placement (reading P6 / step 2): against a k-d tree over the
+    boundary nodes, the lowest index on an exact tie, and a duplicate raises."""
+    from scipy.spatial import cKDTree
+    mesh = O.mesh_from_grid(0.1, (1.0,))
+    nodes, bf = mesh["nodes"], mesh["bfaces"]
+    bn = np.unique(bf)
+    centres = W.fibonacci_points(40, 1.0)
+    got = O.point_electrode_nodes(nodes, bf, centres)
+    d, j = cKDTree(nodes[bn]).query(centres)
+    assert np.allclose(np.linalg.norm(nodes[got] - centres, axis=1), d, atol=1e-15)
+    # a centre exactly halfway between two boundary nodes (h = 1/8: exact coordinates) takes the lower index
+    m8 = O.mesh_from_grid(0.125, (1.0,))
+    n8, b8 = m8["nodes"], m8["bfaces"]
+    bn8 = np.unique(b8)
+    a = bn8[0]
+    b = next(c for c in bn8[1:] if np.sum(n8[c] != n8[a]) == 1 and np.abs(n8[c] - n8[a]).max() == 0.125)
+    mid = 0.5 * (n8[a] + n8[b])
+    dd = np.sum((n8[bn8] - mid) ** 2, axis=1)
+    assert np.sum(dd == dd.min()) >= 2
+    assert O.point_electrode_nodes(n8, b8, mid[None, :])[0] == min(a, b)
+    with pytest.raises(O.OracleError):
+        O.point_electrode_nodes(nodes, bf, np.vstack([centres[:1], centres[:1]]))
