@@ -142,8 +142,8 @@ int zi_mesh_from_surfaces(double h, int n_surf, const int64_t* tri_offset, const
                           double* nodes, int32_t* tets, int32_t* labels, int32_t* bfaces,
                           cudaStream_t stream);
 
-/* Source interpolation (Sec. 2.5: the indices that connect the mesh with the
- * DOFs; Sec. 3.2's nearest-point decomposition): out[i] = the index of the
+/* Source interpolation (Sec. 2.5's index array linking mesh nodes to DOFs;
+ * Sec. 3.2's grouping of DOFs around random centres): out[i] = the index of the
  * source nearest to point i, ties to the lowest index, distances compared as
  * FP64 (dx*dx + dy*dy) + dz*dz with every operation rounded once.
  *   points: device n x 3 f64; sources: device P x 3 f64 (1 <= P < 2^31);

@@ -1,6 +1,6 @@
-"""Plain FP64 CPU oracle of the source interpolation (Sec. 2.5: the indices
-that connect the finite-element mesh with the DOFs; Sec. 3.2 uses the
-same nearest-point rule to decompose the DOFs around random centres).
+"""Plain FP64 CPU oracle of the source interpolation (Sec. 2.5 keeps an index
+array that links mesh nodes to DOFs; Sec. 3.2 groups DOFs around random
+centres by distance).
 
 TEST INFRASTRUCTURE ONLY: the definition the CUDA path of zi_nearest_source
 is checked against.  Only the test suite imports it; it shares no code with

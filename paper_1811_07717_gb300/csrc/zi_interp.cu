@@ -1,7 +1,6 @@
-// Source interpolation (Sec. 2.5: the indices connecting the finite-element
-// mesh with the DOFs; Sec. 3.2 decomposes the DOFs around random centres by
-// the same nearest-point rule): for every point, the nearest DOF position,
-// ties to the lowest index.  Squared distances are formed as
+// Source interpolation (Sec. 2.5 keeps an index array that links mesh nodes
+// to DOFs; Sec. 3.2 groups DOFs around random centres by distance): for
+// every point, the nearest DOF position, ties to the lowest index.  Squared distances are formed as
 // (dx*dx + dy*dy) + dz*dz with every operation rounded once (no contraction),
 // so the comparison, and the index it picks, is exact and reproducible.
 //
