@@ -4,12 +4,11 @@ TEST INFRASTRUCTURE ONLY: a definition for a GPU mesher to be checked
 against.  Only the test suite imports it; it shares no code with the CUDA
 library.
 
-The paper generates a uniform tetrahedral mesh from a surface segmentation:
-each compartment is a closed triangle surface, compartments are processed
-from the innermost (detail) one to the outermost, boundaries may intersect,
-and a per-compartment priority decides the tissue of a tetrahedron whose
-nodes lie in two or more compartments (a lower value is a higher priority).
-The reading taken here:
+Sec. 2.5 builds a uniform tetrahedral mesh out of a surface segmentation: one
+closed triangle surface per compartment, worked through from the inside out;
+surfaces are allowed to cross; when a tetrahedron touches several
+compartments, a number given to each compartment settles which one it joins
+(smaller numbers win).  The reading taken here:
 
 * grid and tets: the Kuhn grid of the sphere mesher (zi_oracle.mesh_from_grid)
   over the cube [-N h, N h]^3, N = ceil(max |coordinate of the outermost
