@@ -71,7 +71,7 @@ def ias_map(L, Y, nu, theta0, beta, hyper, iters):
 def neg_log_posterior(L, y, x, theta, nu, theta0, beta, hyper):
     """The function IAS minimises alternately (up to constants): the Gaussian
     likelihood, the conditionally Gaussian prior x_i ~ N(0, theta_i) and the
-    gamma (G) or inverse-gamma (IG) hyperprior of theta_i."""
+    hyperprior of theta_i, G (a gamma density) or IG (an inverse-gamma one)."""
     r = y - L @ x
     f = 0.5 * (r @ r) / (nu * nu) + np.sum(0.5 * x * x / theta + 0.5 * np.log(theta))
     if hyper == HYPER_G:

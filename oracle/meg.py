@@ -1,5 +1,5 @@
-"""Plain FP64 CPU oracle of the MEG lead field (App. A.2: "derived in an
-analogous way using the Biot-Savart formula").
+"""Plain FP64 CPU oracle of the MEG lead field (App. A.2 points to the
+Biot-Savart law for the magnetic counterpart of the EEG lead field).
 
 TEST INFRASTRUCTURE ONLY: the definition the CUDA path of zi_meg_rhs /
 zi_meg_transfer / zi_meg_leadfield is checked against.  Only the test suite
