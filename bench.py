@@ -530,7 +530,10 @@ def hdiv_workload(args):
     t_stencil = ev_time(lambda: system.source_stencil(pos, dip, zi.SOURCE_PBO10), 5)
     t_sparse = ev_time(lambda: system.leadfield_sparse(Fn, Fw, mixed), 5)
     t_pi = ev_time(lambda: system.leadfield(dip, mixed), 5)
+    ms_apply, bytes_apply = system.time_source_apply(Fn, Fw, reps=5)
     system.close()
+    peak, peak_note = measured_peak_gbs()
+    achieved = bytes_apply / (ms_apply * 1e-3) / 1e9
     line = {"metric": "EEG lead-field build s, Cartesian H(div) sources (PBO 10-source stencil)",
             "value": sec, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": False, "dtype": "f32 inner PCG / f64 refinement, assembly, LF",
@@ -540,6 +543,10 @@ def hdiv_workload(args):
             "cpu_baseline": cpu_leg("hdiv", HDIV_SAMPLE_TEXT, args),
             "source_stencil_s": t_stencil, "leadfield_sparse_s": t_sparse,
             "leadfield_partial_integration_s": t_pi,
+            "roofline": {"bound": "hbm", "kernel": "k_source_apply_ell (H^T = F^T T over the stencil nodes)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_note": peak_note, "traffic": None, "algorithmic_bytes": bytes_apply,
+                         "ms_per_launch": ms_apply},
             "gpu_launches": int(launches), "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 

@@ -451,6 +451,17 @@ int zi_ias_map(const double* L, int32_t Le, int64_t n, const double* Y, int32_t 
 int zi_time_spmm(zi_system* sys, int precision, int reps, double* ms_per_launch,
                  double* bytes_per_launch, cudaStream_t stream);
 
+/* Times the source application of zi_leadfield_sparse (H^T = F^T T, the
+ * kernel that reads the transfer matrix at the source columns' nodes): `reps`
+ * launches on `stream`, each after a 256 MB write that evicts the L2 and
+ * bracketed by CUDA events.  The system must hold T.  Writes the mean launch
+ * time in ms and the algorithmic bytes per launch: the F entries (12 B each),
+ * one read of every distinct T row per group of three columns (one Cartesian
+ * source; per column when ncols is not a multiple of 3), and the write of
+ * H^T (ncols x n_rhs f64). */
+int zi_time_source_apply(zi_system* sys, const int32_t* F_nodes, const double* F_w, int64_t ncols, int K,
+                         int reps, double* ms_per_launch, double* bytes_per_launch, cudaStream_t stream);
+
 /* Number of libzi kernels launched by this process so far (graph replays
  * count each kernel node). */
 int64_t zi_kernel_launches(void);

@@ -10,6 +10,7 @@
 // L = (R S^-1) H.
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -409,6 +410,68 @@ extern "C" int zi_leadfield_sparse(zi_system* S, const int32_t* F_nodes, const d
   }
   if (ncols == 0) return ZI_OK;
   return leadfield_sparse_impl(S, F_nodes, F_w, ncols, K, L, s);
+}
+
+namespace zi {
+namespace {
+__global__ void k_flush_l2(int64_t n, float* __restrict__ buf, float v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    buf[i] = v;
+}
+}  // namespace
+}  // namespace zi
+
+extern "C" int zi_time_source_apply(zi_system* S, const int32_t* F_nodes, const double* F_w, int64_t ncols, int K,
+                                    int reps, double* ms_per_launch, double* bytes_per_launch, cudaStream_t s) {
+  if (!S || !S->has_T) return set_error(ZI_ERR_ARG, "need a system that holds T (run zi_transfer first)");
+  if (ncols < 1 || K < 1 || K > 32 || reps < 1 || !F_nodes || !F_w || !ms_per_launch)
+    return set_error(ZI_ERR_ARG, "bad arguments");
+  const int ncol = S->n_rhs;
+  DevTmp<double> Ht;
+  DevTmp<int> err;
+  DevTmp<float> flush;
+  const int64_t nflush = 64ll << 20;  // 64 Mi floats = 256 MB, twice the L2
+  ZI_CHECK(Ht.alloc((size_t)ncols * ncol, s));
+  ZI_CHECK(err.alloc(1, s));
+  ZI_CHECK(flush.alloc(nflush, s));
+  ZI_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  std::vector<cudaEvent_t> ev(2 * reps);
+  for (auto& e : ev) ZI_CUDA(cudaEventCreate(&e));
+  for (int r = 0; r < reps; ++r) {
+    k_flush_l2<<<sm_count() * 8, 256, 0, s>>>(nflush, flush.p, (float)r);
+    ZI_LAUNCH_CHECK();
+    ZI_CUDA(cudaEventRecord(ev[2 * r], s));
+    ZI_CHECK(source_apply_ell(ncols, K, F_nodes, F_w, S->n, S->T, ncol, Ht.p, err.p, s));
+    ZI_CUDA(cudaEventRecord(ev[2 * r + 1], s));
+  }
+  ZI_CUDA(cudaStreamSynchronize(s));
+  double tot = 0.0;
+  for (int r = 0; r < reps; ++r) {
+    float ms = 0.f;
+    ZI_CUDA(cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]));
+    tot += ms;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  int herr = 0;
+  ZI_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ZI_CUDA(cudaStreamSynchronize(s));
+  ZI_CHECK(device_error_to_status(herr));
+  *ms_per_launch = tot / reps;
+  if (bytes_per_launch) {
+    // distinct T rows per group of columns (a Cartesian source's three columns share their nodes)
+    std::vector<int32_t> fn((size_t)ncols * K);
+    ZI_CUDA(cudaMemcpy(fn.data(), F_nodes, sizeof(int32_t) * fn.size(), cudaMemcpyDeviceToHost));
+    const int64_t grp = (ncols % 3 == 0) ? 3 : 1;
+    double rows = 0.0;
+    std::vector<int32_t> ids;
+    for (int64_t c0 = 0; c0 < ncols; c0 += grp) {
+      ids.assign(fn.begin() + c0 * K, fn.begin() + (c0 + grp) * K);
+      std::sort(ids.begin(), ids.end());
+      rows += (double)(std::unique(ids.begin(), ids.end()) - ids.begin());
+    }
+    *bytes_per_launch = (double)ncols * K * 12.0 + rows * ncol * 8.0 + (double)ncols * ncol * 8.0;
+  }
+  return ZI_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -27,12 +27,12 @@ SOURCE_WHITNEY4, SOURCE_PBO10 = 0, 1
 STENCIL_WIDTH = 8
 
 # Every symbol include/zi.h declares.
-EXPORTS = ("zi_version", "zi_last_error", "zi_status_string", "zi_mesh_from_grid",
-           "zi_locate_dipoles_grid", "zi_mesh_from_surfaces", "zi_nearest_source", "zi_assemble", "zi_system_set_conductivity",
-           "zi_system_get_info", "zi_system_get_matrix", "zi_system_destroy",
-           "zi_solver_opts_default", "zi_transfer", "zi_transfer_batched", "zi_leadfield",
-           "zi_source_stencil", "zi_leadfield_sparse", "zi_source_pi", "zi_meg_rhs",
-           "zi_meg_transfer", "zi_meg_leadfield", "zi_eit_jacobian", "zi_leadfield_noalloc", "zi_ias_map", "zi_time_spmm", "zi_kernel_launches")
+EXPORTS = ("zi_version", "zi_last_error", "zi_status_string", "zi_mesh_from_grid", "zi_locate_dipoles_grid",
+           "zi_mesh_from_surfaces", "zi_nearest_source", "zi_assemble", "zi_system_set_conductivity",
+           "zi_system_get_info", "zi_system_get_matrix", "zi_system_destroy", "zi_solver_opts_default",
+           "zi_transfer", "zi_transfer_batched", "zi_leadfield", "zi_source_stencil", "zi_leadfield_sparse",
+           "zi_source_pi", "zi_meg_rhs", "zi_meg_transfer", "zi_meg_leadfield", "zi_eit_jacobian",
+           "zi_leadfield_noalloc", "zi_ias_map", "zi_time_spmm", "zi_time_source_apply", "zi_kernel_launches")
 
 
 class ZiError(RuntimeError):
@@ -103,6 +103,8 @@ def load_library(path: str = LIB_PATH):
         "zi_leadfield_noalloc": ([P, P, I64, P, P], ctypes.c_int),
         "zi_ias_map": ([P, I32, I64, P, I32, D, D, D, I32, I32, P, P, P], ctypes.c_int),
         "zi_time_spmm": ([P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(D), ctypes.POINTER(D), P], ctypes.c_int),
+        "zi_time_source_apply": ([P, P, P, I64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(D),
+                                  ctypes.POINTER(D), P], ctypes.c_int),
         "zi_kernel_launches": ([], ctypes.c_int64),
     }
     for name, (args, res) in sig.items():
@@ -475,6 +477,17 @@ class System:
         _check(self._lib.zi_eit_jacobian(self._h, _ptr(I), np_, mode, _ptr(gy), _ptr(out), _ptr(y),
                                          ctypes.byref(o), _stream()))
         return y, out
+
+    def time_source_apply(self, F_nodes, F_w, reps=5):
+        """(ms per launch, algorithmic bytes per launch) of the source
+        application of leadfield_sparse (zi_time_source_apply); needs T."""
+        torch = _torch()
+        Fn = _dev(F_nodes, torch.int32).contiguous()
+        Fw = _dev(F_w, torch.float64).contiguous()
+        ms, b = ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.zi_time_source_apply(self._h, _ptr(Fn), _ptr(Fw), Fn.shape[0], Fn.shape[1], int(reps),
+                                              ctypes.byref(ms), ctypes.byref(b), _stream()))
+        return ms.value, b.value
 
     def time_spmm(self, precision=FP64, reps=5):
         """(ms per launch, algorithmic bytes per launch) of the solver's SpMM

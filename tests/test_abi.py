@@ -62,6 +62,8 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.zi_source_stencil(None, None, None, 1, zi.SOURCE_PBO10, 0.0, None, None, None) == zi.ZI_ERR_ARG
     assert lib.zi_leadfield_sparse(None, None, None, 1, 8, None, None, None) == zi.ZI_ERR_ARG
     assert lib.zi_source_pi(None, None, 1, None, None, None) == zi.ZI_ERR_ARG
+    ms = ctypes.c_double()
+    assert lib.zi_time_source_apply(None, None, None, 3, 8, 2, ctypes.byref(ms), None, None) == zi.ZI_ERR_ARG
     assert lib.zi_nearest_source(None, 4, None, 0, None, None) == zi.ZI_ERR_ARG
     assert lib.zi_nearest_source(None, 4, None, 3, None, None) == zi.ZI_ERR_ARG
     toff = (ctypes.c_int64 * 2)(0, 4)

@@ -137,3 +137,24 @@ def test_empty_inputs_of_the_source_and_sensor_calls():
     assert system.meg_leadfield(Tm, sp_, sd, no_pos, Fn, Fw).shape == (4, 0)
     assert zi.nearest_source(no_pos, np.ones((3, 3))).shape == (0,)
     system.close()
+
+
+def test_source_apply_timing_reports_its_algorithmic_bytes():
+    """zi_time_source_apply (the H(div) line's roofline): positive time, and
+    bytes = F entries + distinct T rows per Cartesian source + the H^T write."""
+    spec = W.unit_sphere_point(h=0.1, n_electrodes=16, n_dipoles=200)
+    mesh = zi.mesh_from_grid(spec.h, spec.radii)
+    s6 = W.conductivity(spec, *(mesh[k].cpu().numpy() for k in ("nodes", "tets", "labels")))
+    centres, _ = W.electrode_inputs(spec)
+    pos, _ = W.dipole_inputs(spec)
+    system = zi.System(mesh["nodes"], mesh["tets"], s6, mesh["bfaces"], centres, model="point")
+    system.transfer(zi.SolverOpts(tol=1e-10), want_T=False)
+    dip = zi.locate_dipoles_grid(spec.h, spec.radii, pos)
+    Fn, Fw = system.source_stencil(pos, dip, zi.SOURCE_PBO10)
+    ms, b = system.time_source_apply(Fn, Fw, reps=3)
+    fn = Fn.cpu().numpy()
+    rows = sum(np.unique(fn[3 * p:3 * p + 3]).size for p in range(pos.shape[0]))
+    ncol = spec.n_electrodes - 1
+    assert ms > 0
+    assert b == fn.size * 12.0 + rows * ncol * 8.0 + fn.shape[0] * ncol * 8.0
+    system.close()
