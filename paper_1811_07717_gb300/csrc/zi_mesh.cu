@@ -352,12 +352,13 @@ namespace zi {
 namespace {
 
 constexpr int SEG_MAX_SURF = 64;
-struct SegParams {
-  int C;                              // compartments
-  int rank[SEG_MAX_SURF];             // rank of compartment c
-  int order[SEG_MAX_SURF];            // compartment of rank r
-  int64_t toff[SEG_MAX_SURF + 1];     // triangle range of surface c
-};
+
+// The surface tables live in one small device array of int64 (never in the
+// kernel parameters, and read one entry at a time):
+//   tab[0 .. C]            triangle offsets (surface c: tab[c] .. tab[c+1]-1)
+//   tab[C+1 .. 2C]         rank of compartment c (order by (priority, index))
+//   tab[2C+1 .. 3C]        compartment of rank r
+__host__ __device__ inline int64_t seg_tab_len(int C) { return 3 * (int64_t)C + 1; }
 
 __global__ void k_seg_maxabs(int64_t nv, const double* __restrict__ verts, unsigned long long* __restrict__ out,
                              int* __restrict__ err) {
@@ -372,42 +373,50 @@ __global__ void k_seg_maxabs(int64_t nv, const double* __restrict__ verts, unsig
   }
 }
 
-__global__ void k_seg_labels(Grid g, double h, SegParams sp, int64_t nv, const double* __restrict__ verts,
-                             const int32_t* __restrict__ tris, int32_t* __restrict__ lab, int* __restrict__ err) {
+// Node labels by winding numbers.  Each surface's triangle range starts where
+// the previous one ended, so only the range ends are read (into shared
+// memory, one entry per load).
+__global__ void k_seg_labels(Grid g, double h, int C, const int64_t* __restrict__ tab, int64_t nv, int64_t ntri,
+                             const double* __restrict__ verts, const int32_t* __restrict__ tris,
+                             int32_t* __restrict__ lab, int* __restrict__ err) {
+  __shared__ int64_t s_end[SEG_MAX_SURF];
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    const int64_t e = tab[c + 1];
+    s_end[c] = (e < 0 || e > ntri) ? ntri : e;
+    if (e < 0 || e > ntri) atomicOr(err, DEV_ERR_BAD_INDEX);
+  }
+  __syncthreads();
   const int64_t total = (int64_t)g.G * g.G * g.G;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < total; v += (int64_t)gridDim.x * blockDim.x) {
     const int I = (int)(v / ((int64_t)g.G * g.G));
     const int J = (int)((v / g.G) % g.G);
     const int K = (int)(v % g.G);
-    const double p[3] = {__dmul_rn((double)(I - g.N), h), __dmul_rn((double)(J - g.N), h),
-                         __dmul_rn((double)(K - g.N), h)};
+    const double px = __dmul_rn((double)(I - g.N), h);
+    const double py = __dmul_rn((double)(J - g.N), h);
+    const double pz = __dmul_rn((double)(K - g.N), h);
     int label = -1;
-    for (int c = 0; c < sp.C && label < 0; ++c) {
+    int64_t t = 0;
+    for (int c = 0; c < C && label < 0; ++c) {
+      const int64_t t1 = s_end[c];
       double acc = 0.0;
-      for (int64_t t = sp.toff[c]; t < sp.toff[c + 1]; ++t) {
-        double A[3], B[3], Cv[3];
-        bool ok = true;
-        for (int j = 0; j < 3; ++j) {
-          const int32_t iv = tris[3 * t + j];
-          if (iv < 0 || iv >= nv) {
-            ok = false;
-            break;
-          }
-          double* dst = j == 0 ? A : (j == 1 ? B : Cv);
-          for (int d = 0; d < 3; ++d) dst[d] = verts[3 * (int64_t)iv + d] - p[d];
-        }
-        if (!ok) {
+      for (; t < t1; ++t) {
+        const int32_t i0 = tris[3 * t], i1 = tris[3 * t + 1], i2 = tris[3 * t + 2];
+        if (i0 < 0 || i0 >= nv || i1 < 0 || i1 >= nv || i2 < 0 || i2 >= nv) {
           atomicOr(err, DEV_ERR_BAD_INDEX);
           continue;
         }
-        const double a = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
-        const double b = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
-        const double cc = sqrt(Cv[0] * Cv[0] + Cv[1] * Cv[1] + Cv[2] * Cv[2]);
-        const double num = A[0] * (B[1] * Cv[2] - B[2] * Cv[1]) + A[1] * (B[2] * Cv[0] - B[0] * Cv[2]) +
-                           A[2] * (B[0] * Cv[1] - B[1] * Cv[0]);
-        const double den = a * b * cc + (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) * cc +
-                           (B[0] * Cv[0] + B[1] * Cv[1] + B[2] * Cv[2]) * a +
-                           (Cv[0] * A[0] + Cv[1] * A[1] + Cv[2] * A[2]) * b;
+        const double ax = verts[3 * (int64_t)i0] - px, ay = verts[3 * (int64_t)i0 + 1] - py,
+                     az = verts[3 * (int64_t)i0 + 2] - pz;
+        const double bx = verts[3 * (int64_t)i1] - px, by = verts[3 * (int64_t)i1 + 1] - py,
+                     bz = verts[3 * (int64_t)i1 + 2] - pz;
+        const double cx = verts[3 * (int64_t)i2] - px, cy = verts[3 * (int64_t)i2 + 1] - py,
+                     cz = verts[3 * (int64_t)i2 + 2] - pz;
+        const double a = sqrt(ax * ax + ay * ay + az * az);
+        const double b = sqrt(bx * bx + by * by + bz * bz);
+        const double cc = sqrt(cx * cx + cy * cy + cz * cz);
+        const double num = ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
+        const double den = a * b * cc + (ax * bx + ay * by + az * bz) * cc + (bx * cx + by * cy + bz * cz) * a +
+                           (cx * ax + cy * ay + cz * az) * b;
         acc += 2.0 * atan2(num, den);
       }
       if (acc / (4.0 * 3.14159265358979323846) >= 0.5) label = c;
@@ -416,57 +425,95 @@ __global__ void k_seg_labels(Grid g, double h, SegParams sp, int64_t nv, const d
   }
 }
 
-// Grid coordinates of the four path vertices of Kuhn tet k of cube (I, J, K).
-__device__ __forceinline__ void kuhn_path(int I, int J, int K, int k, int path[4][3]) {
-  int p[3] = {I, J, K};
-  const int a = c_perm[k][0], b = c_perm[k][1];
-  for (int d = 0; d < 3; ++d) path[0][d] = p[d];
-  p[a] += 1;
-  for (int d = 0; d < 3; ++d) path[1][d] = p[d];
-  p[b] += 1;
-  for (int d = 0; d < 3; ++d) path[2][d] = p[d];
-  path[3][0] = I + 1;
-  path[3][1] = J + 1;
-  path[3][2] = K + 1;
+// The segmentation kernels take the Kuhn permutation of a candidate tet from
+// its run-time index k (t mod 6), so they derive its axes by arithmetic
+// instead of reading rows of the constant tables at a run-time index.
+// Axis order of permutation k in lexicographic order (012, 021, 102, 120,
+// 201, 210): a = k / 2, then the smaller (k even) or larger (k odd) of the two
+// other axes; odd permutations are 021, 102, 210.
+__device__ __forceinline__ void perm_axes(int k, int& a, int& b, int& c) {
+  a = k >> 1;
+  const int lo = a == 0 ? 1 : 0, hi = a == 2 ? 1 : 2;
+  b = (k & 1) ? hi : lo;
+  c = 3 - a - b;
+}
+__device__ __forceinline__ int perm_odd(int k) { return (k + (k >> 1)) & 1; }
+__device__ __forceinline__ int perm_index(int a, int b, int c) { return 2 * a + (b > c ? 1 : 0); }
+
+// Path vertex s (0..3) of Kuhn tet k of cube (I, J, K): the cube's first
+// corner, then unit steps along axes a, b, c.
+__device__ __forceinline__ void kuhn_vertex(int I, int J, int K, int k, int s, int& x, int& y, int& z) {
+  int a, b, c;
+  perm_axes(k, a, b, c);
+  x = I + (s >= 1 && a == 0) + (s >= 2 && b == 0) + (s >= 3 && c == 0);
+  y = J + (s >= 1 && a == 1) + (s >= 2 && b == 1) + (s >= 3 && c == 1);
+  z = K + (s >= 1 && a == 2) + (s >= 2 && b == 2) + (s >= 3 && c == 2);
 }
 
-__device__ __forceinline__ int perm_index(int a, int b, int c) {
-  for (int k = 0; k < 6; ++k)
-    if (c_perm[k][0] == a && c_perm[k][1] == b && c_perm[k][2] == c) return k;
-  return 0;
+// Linear index of grid node (x, y, z), or -1 outside the G^3 grid.
+__device__ __forceinline__ int64_t seg_node(const Grid& g, int x, int y, int z) {
+  if (x < 0 || y < 0 || z < 0 || x >= g.G || y >= g.G || z >= g.G) return -1;
+  return ((int64_t)x * g.G + y) * g.G + z;
 }
 
-__global__ void k_seg_tets(Grid g, SegParams sp, const int32_t* __restrict__ lab, int32_t* __restrict__ keep,
-                           int32_t* __restrict__ tlab) {
+__global__ void k_seg_tets(Grid g, int C, const int64_t* __restrict__ tab, const int32_t* __restrict__ lab,
+                           int32_t* __restrict__ keep, int32_t* __restrict__ tlab, int* __restrict__ err) {
+  __shared__ int s_rank[SEG_MAX_SURF], s_order[SEG_MAX_SURF];
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    const int64_t r = tab[C + 1 + c], o = tab[2 * C + 1 + c];
+    const bool bad = r < 0 || r >= C || o < 0 || o >= C;
+    s_rank[c] = bad ? C : (int)r;
+    s_order[c] = bad ? 0 : (int)o;
+    if (bad) atomicOr(err, DEV_ERR_BAD_INDEX);
+  }
+  __syncthreads();
   const int64_t total = 6 * (int64_t)g.Gc * g.Gc * g.Gc;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q = t / 6;
     const int k = (int)(t - 6 * q);
-    const int I = (int)(q / ((int64_t)g.Gc * g.Gc));
-    const int J = (int)((q / g.Gc) % g.Gc);
-    const int K = (int)(q % g.Gc);
-    int path[4][3];
-    kuhn_path(I, J, K, k, path);
-    int best = sp.C;
+    const int I = (int)(q / ((int64_t)g.Gc * g.Gc)), J = (int)((q / g.Gc) % g.Gc), K = (int)(q % g.Gc);
+    int best = C;
+#pragma unroll
     for (int s = 0; s < 4; ++s) {
-      const int l = lab[((int64_t)path[s][0] * g.G + path[s][1]) * g.G + path[s][2]];
-      const int r = l < 0 ? sp.C : sp.rank[l];
+      int x, y, z;
+      kuhn_vertex(I, J, K, k, s, x, y, z);
+      const int64_t lin = seg_node(g, x, y, z);
+      if (lin < 0) {
+        atomicOr(err, DEV_ERR_BAD_INDEX);
+        continue;
+      }
+      const int l = lab[lin];
+      if (l < -1 || l >= C) {
+        atomicOr(err, DEV_ERR_BAD_INDEX);
+        continue;
+      }
+      const int r = l < 0 ? C : s_rank[l];
       best = r < best ? r : best;
     }
-    keep[t] = best < sp.C;
-    tlab[t] = best < sp.C ? sp.order[best] : -1;
+    keep[t] = best < C;
+    tlab[t] = best < C ? s_order[best] : -1;
   }
 }
 
-__global__ void k_seg_used(Grid g, const int32_t* __restrict__ keep, int32_t* __restrict__ used) {
+__global__ void k_seg_used(Grid g, const int32_t* __restrict__ keep, int32_t* __restrict__ used,
+                           int* __restrict__ err) {
   const int64_t total = 6 * (int64_t)g.Gc * g.Gc * g.Gc;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     if (!keep[t]) continue;
     const int64_t q = t / 6;
     const int k = (int)(t - 6 * q);
-    int path[4][3];
-    kuhn_path((int)(q / ((int64_t)g.Gc * g.Gc)), (int)((q / g.Gc) % g.Gc), (int)(q % g.Gc), k, path);
-    for (int s = 0; s < 4; ++s) used[((int64_t)path[s][0] * g.G + path[s][1]) * g.G + path[s][2]] = 1;
+    const int I = (int)(q / ((int64_t)g.Gc * g.Gc)), J = (int)((q / g.Gc) % g.Gc), K = (int)(q % g.Gc);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      int x, y, z;
+      kuhn_vertex(I, J, K, k, s, x, y, z);
+      const int64_t lin = seg_node(g, x, y, z);
+      if (lin < 0) {
+        atomicOr(err, DEV_ERR_BAD_INDEX);
+        continue;
+      }
+      used[lin] = 1;
+    }
   }
 }
 
@@ -475,29 +522,39 @@ __device__ __forceinline__ int seg_kept(const Grid& g, const int32_t* keep, int 
   return keep[6 * (((int64_t)I * g.Gc + J) * g.Gc + K) + k];
 }
 
-// Boundary-face mask of kept candidate tet k of cube (I, J, K), by stored local face.
+// Boundary-face mask of kept candidate tet k of cube (I, J, K), by stored
+// local face (bit f: face f is on the boundary).  The neighbour across the
+// face opposite path vertex 0 is tet (b, c, a) of cube +e_a, opposite path
+// vertex 3 tet (c, a, b) of cube -e_c, opposite path vertices 1 and 2 the
+// tets (b, a, c) and (a, c, b) of the same cube; for an odd permutation the
+// stored faces 2 and 3 are opposite path vertices 3 and 2.
 __device__ __forceinline__ int seg_bmask(const Grid& g, const int32_t* keep, int I, int J, int K, int k) {
-  const int a = c_perm[k][0], b = c_perm[k][1], c = c_perm[k][2];
-  int nb[4];
-  int qa[3] = {I, J, K};
-  qa[a] += 1;
-  nb[0] = seg_kept(g, keep, qa[0], qa[1], qa[2], perm_index(b, c, a));
-  nb[1] = seg_kept(g, keep, I, J, K, perm_index(b, a, c));
-  nb[2] = seg_kept(g, keep, I, J, K, perm_index(a, c, b));
-  int qc[3] = {I, J, K};
-  qc[c] -= 1;
-  nb[3] = seg_kept(g, keep, qc[0], qc[1], qc[2], perm_index(c, a, b));
-  int m = 0;
-  for (int f = 0; f < 4; ++f) {
-    const int pv = c_odd[k] ? (f == 2 ? 3 : (f == 3 ? 2 : f)) : f;  // path vertex opposite stored face f
-    if (!nb[pv]) m |= 1 << f;
-  }
-  return m;
+  int a, b, c;
+  perm_axes(k, a, b, c);
+  const int n0 = seg_kept(g, keep, I + (a == 0), J + (a == 1), K + (a == 2), perm_index(b, c, a));
+  const int n1 = seg_kept(g, keep, I, J, K, perm_index(b, a, c));
+  const int n2 = seg_kept(g, keep, I, J, K, perm_index(a, c, b));
+  const int n3 = seg_kept(g, keep, I - (c == 0), J - (c == 1), K - (c == 2), perm_index(c, a, b));
+  const bool odd = perm_odd(k);
+  const int f2 = odd ? n3 : n2, f3 = odd ? n2 : n3;
+  return (n0 ? 0 : 1) | (n1 ? 0 : 2) | (f2 ? 0 : 4) | (f3 ? 0 : 8);
 }
 
+// Vertices of the outward local face f of a positively oriented tet (face f
+// opposite vertex f): {1,2,3}, {0,3,2}, {0,1,3}, {0,2,1}.
+__device__ __forceinline__ void tet_face(int f, int& u, int& v, int& w) {
+  u = f == 0 ? 1 : 0;
+  v = f == 0 ? 2 : (f == 1 ? 3 : (f == 2 ? 1 : 2));
+  w = f == 0 ? 3 : (f == 1 ? 2 : (f == 2 ? 3 : 1));
+}
+
+// Kept tets with their labels (output call) and boundary-face counts.  toff
+// and nid come from scans of keep and used, so o < m and every node id of a
+// kept tet is < n; the node index is still checked.
 __global__ void k_seg_out(Grid g, const int32_t* __restrict__ keep, const int32_t* __restrict__ tlab,
                           const int32_t* __restrict__ toff, const int32_t* __restrict__ nid,
-                          int32_t* __restrict__ tets, int32_t* __restrict__ labels, int32_t* __restrict__ bcnt) {
+                          int32_t* __restrict__ tets, int32_t* __restrict__ labels, int32_t* __restrict__ bcnt,
+                          int* __restrict__ err) {
   const int64_t total = 6 * (int64_t)g.Gc * g.Gc * g.Gc;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     if (!keep[t]) continue;
@@ -508,16 +565,22 @@ __global__ void k_seg_out(Grid g, const int32_t* __restrict__ keep, const int32_
     const int K = (int)(q % g.Gc);
     const int64_t o = toff[t];
     if (tets) {
-      int path[4][3];
-      kuhn_path(I, J, K, k, path);
       int32_t v[4];
-      for (int s = 0; s < 4; ++s) v[s] = nid[((int64_t)path[s][0] * g.G + path[s][1]) * g.G + path[s][2]];
-      if (c_odd[k]) {
-        const int32_t x = v[2];
-        v[2] = v[3];
-        v[3] = x;
+      bool ok = true;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        int x, y, z;
+        kuhn_vertex(I, J, K, k, s, x, y, z);
+        const int64_t lin = seg_node(g, x, y, z);
+        ok = ok && lin >= 0;
+        v[s] = lin >= 0 ? nid[lin] : -1;
       }
-      for (int s = 0; s < 4; ++s) tets[4 * o + s] = v[s];
+      if (!ok) atomicOr(err, DEV_ERR_BAD_INDEX);
+      const bool odd = perm_odd(k);
+      tets[4 * o + 0] = v[0];
+      tets[4 * o + 1] = v[1];
+      tets[4 * o + 2] = odd ? v[3] : v[2];
+      tets[4 * o + 3] = odd ? v[2] : v[3];
       labels[o] = tlab[t];
     }
     bcnt[o] = __popc(seg_bmask(g, keep, I, J, K, k));
@@ -537,17 +600,27 @@ __global__ void k_seg_bfaces(Grid g, const int32_t* __restrict__ keep, const int
     if (!msk) continue;
     const int64_t o = toff[t];
     int64_t b = boff[o];
+#pragma unroll
     for (int f = 0; f < 4; ++f) {
       if (!(msk >> f & 1)) continue;
-      for (int j = 0; j < 3; ++j) bfaces[3 * b + j] = tets[4 * o + c_face[f][j]];
+      int u, v, w;
+      tet_face(f, u, v, w);
+      bfaces[3 * b + 0] = tets[4 * o + u];
+      bfaces[3 * b + 1] = tets[4 * o + v];
+      bfaces[3 * b + 2] = tets[4 * o + w];
       ++b;
     }
   }
 }
 
+inline bool misaligned(const void* p, size_t a) { return ((uintptr_t)p % a) != 0; }
+
 }  // namespace
 }  // namespace zi
 
+// The mesher is set-up work, so each kernel is followed by a stream
+// synchronisation: a device error is then reported at the line of the kernel
+// that raised it.
 extern "C" int zi_mesh_from_surfaces(double h, int n_surf, const int64_t* tri_offset, const int32_t* priority,
                                      const double* verts, int64_t nv, const int32_t* tris, int64_t* n_nodes,
                                      int64_t* n_tets, int64_t* n_bfaces, double* nodes, int32_t* tets,
@@ -558,30 +631,44 @@ extern "C" int zi_mesh_from_surfaces(double h, int n_surf, const int64_t* tri_of
   if (!(h > 0) || !isfinite(h)) return set_error(ZI_ERR_ARG, "grid step h must be positive and finite");
   if (n_surf < 1 || n_surf > SEG_MAX_SURF) return set_error(ZI_ERR_ARG, "need 1..%d surfaces", SEG_MAX_SURF);
   if (!tri_offset || !priority || !verts || !tris || nv < 3) return set_error(ZI_ERR_ARG, "null or empty surface input");
-  SegParams sp;
-  sp.C = n_surf;
+  if (nv > INT32_MAX) return set_error(ZI_ERR_ARG, "too many surface vertices for int32 triangle indices");
+  if (misaligned(verts, 8) || misaligned(tris, 4) || misaligned(nodes, 8) || misaligned(tets, 4) ||
+      misaligned(labels, 4) || misaligned(bfaces, 4))
+    return set_error(ZI_ERR_ARG, "arrays must be aligned to their element size");
   if (tri_offset[0] != 0) return set_error(ZI_ERR_ARG, "tri_offset[0] must be 0");
-  for (int c = 0; c <= n_surf; ++c) {
-    sp.toff[c] = tri_offset[c];
+  const int C = n_surf;
+  std::vector<int64_t> tab(seg_tab_len(C));
+  for (int c = 0; c <= C; ++c) {
     if (c && !(tri_offset[c] > tri_offset[c - 1])) return set_error(ZI_ERR_ARG, "every surface needs triangles");
+    tab[c] = tri_offset[c];
   }
+  const int64_t ntri = tri_offset[C];
+  if (ntri > INT64_MAX / 3) return set_error(ZI_ERR_ARG, "too many triangles");
   // ranks: order by (priority, index)
-  for (int c = 0; c < n_surf; ++c) sp.order[c] = c;
-  for (int i = 1; i < n_surf; ++i)
+  std::vector<int> order(C), rank(C);
+  for (int c = 0; c < C; ++c) order[c] = c;
+  for (int i = 1; i < C; ++i)
     for (int j = i; j > 0; --j) {
-      const int x = sp.order[j - 1], y = sp.order[j];
+      const int x = order[j - 1], y = order[j];
       if (priority[y] < priority[x] || (priority[y] == priority[x] && y < x)) {
-        sp.order[j - 1] = y;
-        sp.order[j] = x;
+        order[j - 1] = y;
+        order[j] = x;
       }
     }
-  for (int r = 0; r < n_surf; ++r) sp.rank[sp.order[r]] = r;
+  for (int r = 0; r < C; ++r) rank[order[r]] = r;
+  for (int c = 0; c < C; ++c) {
+    tab[C + 1 + c] = rank[c];
+    tab[2 * C + 1 + c] = order[c];
+  }
   DevTmp<unsigned long long> mx;
   DevTmp<int> err;
+  DevTmp<int64_t> dtab;
   ZI_CHECK(mx.alloc(1, s));
   ZI_CHECK(err.alloc(1, s));
+  ZI_CHECK(dtab.alloc(tab.size(), s));
   ZI_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), s));
   ZI_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  ZI_CUDA(cudaMemcpyAsync(dtab.p, tab.data(), sizeof(int64_t) * tab.size(), cudaMemcpyHostToDevice, s));
   k_seg_maxabs<<<grid_for(3 * nv, 256), 256, 0, s>>>(nv, verts, mx.p, err.p);
   ZI_LAUNCH_CHECK();
   unsigned long long bits = 0;
@@ -607,17 +694,26 @@ extern "C" int zi_mesh_from_surfaces(double h, int n_surf, const int64_t* tri_of
   ZI_CHECK(used.alloc(nvg, s));
   ZI_CHECK(nid.alloc(nvg + 1, s));
   ZI_CHECK(toff.alloc(ncand + 1, s));
-  k_seg_labels<<<grid_for(nvg, 128, 152u * 64u), 128, 0, s>>>(g, h, sp, nv, verts, tris, lab.p, err.p);
+  k_seg_labels<<<grid_for(nvg, 128, 152u * 64u), 128, 0, s>>>(g, h, C, dtab.p, nv, ntri, verts, tris, lab.p,
+                                                                err.p);
   ZI_LAUNCH_CHECK();
-  k_seg_tets<<<grid_for(ncand, 256), 256, 0, s>>>(g, sp, lab.p, keep.p, tlab.p);
+  ZI_CUDA(cudaStreamSynchronize(s));
+  k_seg_tets<<<grid_for(ncand, 256), 256, 0, s>>>(g, C, dtab.p, lab.p, keep.p, tlab.p, err.p);
   ZI_LAUNCH_CHECK();
+  ZI_CUDA(cudaStreamSynchronize(s));
   ZI_CUDA(cudaMemsetAsync(used.p, 0, sizeof(int32_t) * nvg, s));
-  k_seg_used<<<grid_for(ncand, 256), 256, 0, s>>>(g, keep.p, used.p);
+  k_seg_used<<<grid_for(ncand, 256), 256, 0, s>>>(g, keep.p, used.p, err.p);
   ZI_LAUNCH_CHECK();
+  ZI_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ZI_CUDA(cudaStreamSynchronize(s));
+  ZI_CHECK(device_error_to_status(herr));
   int64_t n = 0, m = 0, nb = 0;
   ZI_CHECK(exclusive_scan_i32(used.p, nid.p, nvg, &n, s));
   ZI_CHECK(exclusive_scan_i32(keep.p, toff.p, ncand, &m, s));
   if (m > INT32_MAX / 4) return set_error(ZI_ERR_ARG, "mesh too large for int32 indices");
+  // the output call writes into arrays sized by the counting call's counts
+  if (outs && (*n_nodes != n || *n_tets != m))
+    return set_error(ZI_ERR_ARG, "pass the counts of the counting call in n_nodes and n_tets");
   ZI_CHECK(bcnt.alloc(m, s));
   ZI_CHECK(boff.alloc(m + 1, s));
   // the boundary faces read the tets back, so the counting call keeps its own copy
@@ -630,14 +726,17 @@ extern "C" int zi_mesh_from_surfaces(double h, int n_surf, const int64_t* tri_of
     tets_w = tets_tmp.p;
     labels_w = labels_tmp.p;
   }
-  k_seg_out<<<grid_for(ncand, 256), 256, 0, s>>>(g, keep.p, tlab.p, toff.p, nid.p, tets_w, labels_w, bcnt.p);
+  k_seg_out<<<grid_for(ncand, 256), 256, 0, s>>>(g, keep.p, tlab.p, toff.p, nid.p, tets_w, labels_w, bcnt.p,
+                                                   err.p);
   ZI_LAUNCH_CHECK();
+  ZI_CUDA(cudaStreamSynchronize(s));
   ZI_CHECK(exclusive_scan_i32(bcnt.p, boff.p, m, &nb, s));
   if (outs && *n_bfaces != nb)
     return set_error(ZI_ERR_ARG, "pass the count of the counting call in n_bfaces");
   if (outs) {
     k_nodes_out<<<grid_for(nvg, 256), 256, 0, s>>>(g, h, used.p, nid.p, nodes);
     ZI_LAUNCH_CHECK();
+    ZI_CUDA(cudaStreamSynchronize(s));
     k_seg_bfaces<<<grid_for(ncand, 256), 256, 0, s>>>(g, keep.p, toff.p, boff.p, tets, bfaces);
     ZI_LAUNCH_CHECK();
   }
