@@ -1,11 +1,13 @@
 """Lead-field build benchmark on GB300.
 
-One step = one whole LF build of the three-shell head at h = 2 mm
-(428,185 nodes, 2,447,424 tets, 128 complete-model electrodes, 20,000
-dipoles x 3 orientations): dipole location, assembly (element stiffness,
-pattern, CEM terms, grounding), T = A^-1 B by multi-RHS PCG to a relative
-residual of 1e-10 per column, source application and the electrode Schur
-step, from inputs resident in HBM to L (128 x 60,000) in HBM.
+One step = one whole LF build of the three-shell head at h = 1 mm with a
+transversely anisotropic skull (3,342,701 nodes, 19,573,872 tets, 256
+complete-model electrodes, 100,000 dipoles x 3 orientations): dipole
+location, assembly (element stiffness, pattern, CEM terms, grounding),
+T = A^-1 B by multi-RHS PCG to a relative residual of 1e-10 per column,
+source application and the electrode Schur step, from inputs resident in HBM
+to L (256 x 300,000) in HBM.  (--workload shell2mm: the 2 mm isotropic head
+with 128 electrodes and 20,000 dipoles.)
 
 The headline is the mixed-precision build (FP32 inner PCG inside FP64
 iterative refinement); the plain FP64 PCG build on the same GPU is reported
@@ -35,25 +37,44 @@ import numpy as np  # noqa: E402
 
 METRIC = "LF build s, mixed vs FP64 PCG at rel.err<=1e-6 on 1 GB300; SpMM HBM GB/s vs peak"
 UNIT = "s"
-WORKLOAD = "three-shell sphere 80/86/92 mm, h=2 mm Kuhn grid (428185 nodes, 2447424 tets), " \
-           "128 CEM electrodes r=5 mm z=2e-3 Ohm m^2, 20000 dipoles x 3, PCG tol 1e-10"
+WORKLOADS = {
+    "aniso1mm": ("config_three_shell_1mm_aniso",
+                 "three-shell sphere 80/86/92 mm, h=1 mm Kuhn grid (3342701 nodes, 19573872 tets), transversely "
+                 "anisotropic skull (radial 0.00132, tangential 0.0132 S/m), 256 CEM electrodes r=5 mm "
+                 "z=2e-3 Ohm m^2, 100000 dipoles x 3, PCG tol 1e-10"),
+    "shell2mm": ("config_three_shell_2mm",
+                 "three-shell sphere 80/86/92 mm, h=2 mm Kuhn grid (428185 nodes, 2447424 tets), "
+                 "128 CEM electrodes r=5 mm z=2e-3 Ohm m^2, 20000 dipoles x 3, PCG tol 1e-10"),
+}
+DEFAULT_WORKLOAD = "aniso1mm"
 # ncu DRAM traffic per launch of the FP32 SpMM on this workload, from the capture
 # summarised in profiles/ (None until taken, or once the kernel source changed).
-SPMM_TRAFFIC = {"source_sha": "8e30f73bd16fd9df", "bytes": 246.94656e6 + 184.47488e6}
+SPMM_TRAFFIC = {
+    "shell2mm": {"source_sha": "8e30f73bd16fd9df", "bytes": 246.94656e6 + 184.47488e6,
+                 "note": "one ncu capture of the standalone launch on this workload"},
+}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison build")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="shell2mm", choices=["shell2mm", "aniso1mm", "batch", "ias", "eit", "hdiv", "meg", "segmesh"],
-                    help="shell2mm: the headline workload; aniso1mm: 1 mm anisotropic-skull head, 256 "
-                         "electrodes, 100k dipoles; batch: 24 heads, batched vs per-head solves")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=["aniso1mm", "shell2mm", "batch", "ias", "eit", "hdiv", "meg", "segmesh", "spmm"],
+                    help="aniso1mm (default, the precision workload): 1 mm anisotropic-skull head, 256 "
+                         "electrodes, 100k dipoles; shell2mm: 2 mm head, 128 electrodes, 20k dipoles; batch: 24 "
+                         "heads, batched vs per-head solves; spmm: the solver's SpMM launched on its own (for a "
+                         "profiler), see --h/--electrodes/--precision")
+    ap.add_argument("--h", type=float, default=0.002, help="spmm: grid step of the three-shell head (m)")
+    ap.add_argument("--electrodes", type=int, default=128, help="spmm: CEM electrodes (right-hand sides)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="spmm: which SpMM")
+    ap.add_argument("--aniso", action="store_true", help="spmm: transversely anisotropic skull")
+    ap.add_argument("--reps", type=int, default=3, help="spmm: standalone launches")
     return ap.parse_args()
 
 
@@ -80,22 +101,85 @@ ORACLE_SAMPLE = dict(h=0.004, electrodes=128, dipoles=20000)
 ORACLE_SAMPLE_TEXT = ("oracle LF build (numpy + SuperLU direct solve, 1 thread) of the same three-shell head, "
                       "128 CEM electrodes and 20000 dipoles at h=4 mm (56235 nodes): the h=2 mm direct "
                       "factorisation does not fit a bounded CPU sample")
+# the direct-solve sample of each LF workload: the same head at h = 4 mm
+DIRECT_SAMPLES = {
+    "shell2mm": ("W.three_shell(0.004, 128, 20000, seed=2)", ORACLE_SAMPLE_TEXT),
+    "aniso1mm": ("W.three_shell(0.004, 256, 20000, seed=3, skull_aniso=(0.00132, 0.0132))",
+                 "oracle LF build (numpy + SuperLU direct solve, 1 thread) of the same anisotropic-skull "
+                 "three-shell head, 256 CEM electrodes and 20000 dipoles at h=4 mm (56235 nodes): a direct "
+                 "factorisation at h=1 mm does not fit a bounded CPU sample"),
+}
 
 
-def oracle_once() -> float:
-    """One oracle LF build of the sample, in a fresh single-threaded process
-    (spawned with exec, so it never inherits a CUDA context)."""
+def oracle_once(workload: str = "shell2mm") -> float:
+    """One oracle LF build of the workload's h = 4 mm sample, in a fresh
+    single-threaded process (spawned with exec, so it never inherits a CUDA
+    context)."""
     code = ("import sys,time; sys.path.insert(0, %r)\n"
             "from oracle import zi_oracle as O\n"
             "from paper_1811_07717_gb300 import workloads as W\n"
-            "spec = W.three_shell(%r, %d, %d, seed=2)\n"
+            "spec = %s\n"
             "t = time.perf_counter(); O.leadfield_from_spec(spec, W); print(time.perf_counter() - t)\n"
-            % (ROOT, ORACLE_SAMPLE["h"], ORACLE_SAMPLE["electrodes"], ORACLE_SAMPLE["dipoles"]))
+            % (ROOT, DIRECT_SAMPLES[workload][0]))
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-500:])
     return float(r.stdout.strip().splitlines()[-1])
+
+
+# CPU block PCG of the full workload (oracle/cpu_pcg.c, FP64, Jacobi, OpenMP over
+# every host core) on the oracle's own assembly of the workload's system.
+# A full solve of the 1 mm head takes minutes, so a step is bounded: the time
+# of one iteration is the difference of two capped runs (K2 and K1
+# iterations; allocation, first touch and set-up cancel), and the iteration
+# count is the CPU's own, from a full solve of an evenly spaced sample of the
+# columns.  LF seconds = s per iteration x that count (the transfer solve is
+# all but a few percent of the LF build).
+CPU_PCG_K1, CPU_PCG_K2, CPU_PCG_COLS = 1, 6, 8
+
+
+def cpu_pcg_text(workload: str) -> str:
+    return ("CPU block PCG (oracle/cpu_pcg.c: FP64 Jacobi PCG, OpenMP, all host cores) on the oracle's own "
+            "assembly of the full workload: seconds per iteration with all %s columns (difference of %d- and "
+            "%d-iteration runs) x the CPU's own iteration count to tol 1e-10 (the largest of a full solve of %d "
+            "evenly spaced columns); the transfer solve only"
+            % ({"aniso1mm": 256, "shell2mm": 128}[workload], CPU_PCG_K2, CPU_PCG_K1, CPU_PCG_COLS))
+
+
+def cpu_pcg_workload(workload: str, steps: int) -> dict:
+    """Runs the CPU block PCG measurement of the workload in a fresh process:
+    `steps` per-iteration times, the sampled iteration count, threads."""
+    code = ("import sys,time,os,json; import numpy as np; sys.path.insert(0, %r)\n"
+            "from oracle import zi_oracle as O, cpu_pcg\n"
+            "from paper_1811_07717_gb300 import workloads as W\n"
+            "spec = W.%s()\n"
+            "t0 = time.perf_counter()\n"
+            "mesh = O.mesh_from_grid(spec.h, spec.radii)\n"
+            "s6 = W.conductivity(spec, mesh['nodes'], mesh['tets'], mesh['labels'])\n"
+            "c, z = W.electrode_inputs(spec)\n"
+            "S = O.System(mesh, s6, c, spec.electrode_model, radius=spec.electrode_radius, z=z)\n"
+            "A, B = S.A.tocsr(), np.ascontiguousarray(S.B)\n"
+            "del mesh, s6\n"
+            "setup = time.perf_counter() - t0\n"
+            "th = len(os.sched_getaffinity(0))\n"
+            "cols = np.unique(np.linspace(0, B.shape[1] - 1, %d).round().astype(int))\n"
+            "t = time.perf_counter(); _, its, kmax = cpu_pcg.block_pcg(A, np.ascontiguousarray(B[:, cols]), "
+            "tol=1e-10, threads=th); t_sample = time.perf_counter() - t\n"
+            "def run(k):\n"
+            "    t = time.perf_counter(); cpu_pcg.block_pcg(A, B, tol=1e-10, maxit=k, threads=th)\n"
+            "    return time.perf_counter() - t\n"
+            "per = []\n"
+            "for _ in range(%d):\n"
+            "    a = run(%d); b = run(%d); per.append((b - a) / %d)\n"
+            "print(json.dumps({'s_per_iteration': per, 'iterations': int(kmax), 'threads': th, 'setup_s': setup, "
+            "'sample_columns': int(cols.size), 'sample_solve_s': t_sample}))\n"
+            % (ROOT, WORKLOADS[workload][0], CPU_PCG_COLS, max(1, steps), CPU_PCG_K1, CPU_PCG_K2,
+               CPU_PCG_K2 - CPU_PCG_K1))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("cpu PCG measurement failed: " + r.stderr[-500:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 HDIV_SAMPLE_TEXT = ("oracle LF build with PBO 10-source H(div) sources (numpy stencils and KKT solves + SuperLU "
@@ -133,68 +217,27 @@ def oracle_sample_once(kind: str) -> float:
     return float(r.stdout.strip().splitlines()[-1])
 
 
-def cpu_pcg_once() -> dict:
-    """The CPU block PCG baseline (oracle/cpu_pcg.c: the same Jacobi PCG,
-    FP64, OpenMP over all host cores) on the oracle sample's matrix, in a
-    fresh process: seconds, iterations and threads of one transfer solve."""
-    code = ("import sys,time,os,json; sys.path.insert(0, %r)\n"
-            "from oracle import zi_oracle as O, cpu_pcg\n"
-            "from paper_1811_07717_gb300 import workloads as W\n"
-            "spec = W.three_shell(%r, %d, 10, seed=2)\n"
-            "mesh = O.mesh_from_grid(spec.h, spec.radii)\n"
-            "s6 = W.conductivity(spec, mesh['nodes'], mesh['tets'], mesh['labels'])\n"
-            "c, z = W.electrode_inputs(spec)\n"
-            "S = O.System(mesh, s6, c, spec.electrode_model, radius=spec.electrode_radius, z=z)\n"
-            "th = len(os.sched_getaffinity(0))\n"
-            "cpu_pcg.block_pcg(S.A, S.B, tol=1e-10, maxit=3, threads=th)\n"
-            "t = time.perf_counter(); T, it, k = cpu_pcg.block_pcg(S.A, S.B, tol=1e-10, threads=th)\n"
-            "print(json.dumps({'s': time.perf_counter() - t, 'iterations': int(k), 'threads': th}))\n"
-            % (ROOT, ORACLE_SAMPLE["h"], ORACLE_SAMPLE["electrodes"]))
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("cpu PCG sample failed: " + r.stderr[-500:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
-
-
-def gpu_fp64_same_sample() -> dict:
-    """The GPU FP64 transfer solve of the CPU PCG's sample (same head, same
-    tolerance), for the per-iteration comparison."""
-    import torch
-    from paper_1811_07717_gb300 import workloads as W
-    from paper_1811_07717_gb300 import zi
-    spec = W.three_shell(ORACLE_SAMPLE["h"], ORACLE_SAMPLE["electrodes"], 10, seed=2)
-    mesh = zi.mesh_from_grid(spec.h, spec.radii)
-    s6 = W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(),
-                        mesh["labels"].cpu().numpy())
-    centres, z = W.electrode_inputs(spec)
-    system = zi.System(mesh["nodes"], mesh["tets"], s6, mesh["bfaces"], centres, model="cem", z=z,
-                       radius=spec.electrode_radius)
-    opts = zi.SolverOpts(tol=1e-10)
-    system.transfer(opts, want_T=False)
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    t0.record()
-    _, it, _ = system.transfer(opts, want_T=False)
-    t1.record()
-    torch.cuda.synchronize()
-    system.close()
-    return {"s": t0.elapsed_time(t1) / 1e3, "iterations": int(it.max())}
-
-
 def reference_arm(args):
+    """The oracle as it stands, on this machine's host cores, on the bench's own
+    workload: the CPU block PCG of oracle/cpu_pcg.c on the oracle's assembly
+    (rank 0 alone; the other ranks exit without work)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        oracle_once()
-    ts = [oracle_once() for _ in range(max(1, args.steps))]
-    v = statistics.mean(ts)
+    wl = args.workload if args.workload in WORKLOADS else DEFAULT_WORKLOAD
+    m = cpu_pcg_workload(wl, args.warmup + max(1, args.steps))
+    per = m["s_per_iteration"][args.warmup:] or m["s_per_iteration"]
+    v = statistics.mean(per) * m["iterations"]
+    text = cpu_pcg_text(wl)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": ORACLE_SAMPLE_TEXT},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE_TEXT},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": WORKLOADS[wl][1], "sample": text},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": m["threads"], "kind": "oracle", "sample": text},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "cpu_pcg": {"s_per_iteration": per, "iterations": m["iterations"], "threads": m["threads"],
+                        "setup_s": m["setup_s"], "sample_columns": m["sample_columns"],
+                        "sample_solve_s": m["sample_solve_s"]}}
     print(json.dumps(line), flush=True)
 
 
@@ -668,6 +711,38 @@ def segmesh_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def spmm_workload(args):
+    """The solver's SpMM on its own, for a profiler: builds one three-shell
+    head's system, runs one CG iteration so the work vectors and the solver's
+    matrix copies exist, then launches the SpMM `--reps` times after an L2
+    flush (zi_time_spmm).  The first SpMM launch belongs to the one-iteration
+    solve; select the standalone ones with ncu -s 1.  Prints the CUDA-event
+    time per launch and the algorithmic bytes."""
+    import torch
+    from paper_1811_07717_gb300 import workloads as W
+    from paper_1811_07717_gb300 import _build, zi
+    _build.build()
+    spec = W.three_shell(args.h, args.electrodes, 10, seed=2,
+                         skull_aniso=(0.00132, 0.0132) if args.aniso else None)
+    mesh = zi.mesh_from_grid(spec.h, spec.radii)
+    s6 = W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(),
+                        mesh["labels"].cpu().numpy())
+    centres, z = W.electrode_inputs(spec)
+    system = zi.System(mesh["nodes"], mesh["tets"], s6, mesh["bfaces"], centres, model="cem", z=z,
+                       radius=spec.electrode_radius)
+    prec = zi.MIXED if args.precision == "mixed" else zi.FP64
+    opts = zi.SolverOpts(tol=1e-10, precision=prec, maxit=1, check_every=1, max_outer=1)
+    system.transfer(opts, want_T=False, allow_not_converged=True)
+    ms, by = system.time_spmm(prec, reps=args.reps)
+    torch.cuda.synchronize()
+    info = system.info()
+    print(json.dumps({"workload": "spmm", "h": args.h, "aniso": bool(args.aniso), "n": info["n"],
+                      "nnz": info["nnz"], "ncol": info["n_rhs"], "precision": args.precision,
+                      "spmm_kernel": info.get("spmm_kernel"), "ms_per_launch": ms, "algorithmic_bytes": by,
+                      "GBps": by / ms / 1e6}), flush=True)
+    system.close()
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -691,7 +766,7 @@ def main():
     _build.build()
 
     if args.workload not in ("shell2mm", "aniso1mm") and world > 1:
-        # the single-GPU workloads (batch, IAS, EIT, H(div), MEG, mesher) run on rank 0 alone
+        # the single-GPU workloads (batch, IAS, EIT, H(div), MEG, mesher, SpMM) run on rank 0 alone
         if rank != 0:
             dist.destroy_process_group()
             return
@@ -707,11 +782,10 @@ def main():
         return meg_workload(args)
     if args.workload == "segmesh":
         return segmesh_workload(args)
-    spec = W.config_three_shell_2mm() if args.workload == "shell2mm" else W.config_three_shell_1mm_aniso()
-    workload = WORKLOAD if args.workload == "shell2mm" else (
-        "three-shell sphere 80/86/92 mm, h=1 mm Kuhn grid (3342701 nodes, 19573872 tets), transversely "
-        "anisotropic skull (radial 0.00132, tangential 0.0132 S/m), 256 CEM electrodes, 100000 dipoles x 3, "
-        "PCG tol 1e-10")
+    if args.workload == "spmm":
+        return spmm_workload(args)
+    spec = getattr(W, WORKLOADS[args.workload][0])()
+    workload = WORKLOADS[args.workload][1]
     dev = torch.device("cuda", local)
     mesh = zi.mesh_from_grid(spec.h, spec.radii)
     s6 = W.conductivity(spec, mesh["nodes"].cpu().numpy(), mesh["tets"].cpu().numpy(), mesh["labels"].cpu().numpy())
@@ -769,6 +843,7 @@ def main():
     system = zi.System(d["nodes"], d["tets"], d["s6"], d["bfaces"], d["centres"], model="cem", z=d["z"],
                        radius=spec.electrode_radius)
     _, it_mixed, rr_mixed = system.transfer(mixed, want_T=False)
+    sinfo = system.solver_info()
     ms32, bytes32 = system.time_spmm(zi.MIXED, reps=5)
     it64 = None
     if not args.no_fp64:
@@ -779,12 +854,15 @@ def main():
     system.close()
     peak, peak_note = measured_peak_gbs()
     achieved = bytes32 / (ms32 * 1e-3) / 1e9
-    traffic = (SPMM_TRAFFIC["bytes"] if SPMM_TRAFFIC["source_sha"] == spmm_source_sha()
-               and args.workload == "shell2mm" else None)
-    roofline = {"bound": "hbm", "kernel": "k_spmm_ell<1, false> (FP32 ELL SpMM fused with the p.q column dots)",
+    cap = SPMM_TRAFFIC.get(args.workload)
+    traffic = cap["bytes"] if cap and cap["source_sha"] == spmm_source_sha() else None
+    kname = {zi.SPMM32_ELL: "k_spmm_ell<%d, false>", zi.SPMM32_ELL_OVERFLOW: "k_spmm_ell<%d, true>"}.get(
+        sinfo["spmm32"], "k_spmm_ell<%d, ?>") % sinfo["vectors_per_thread32"]
+    roofline = {"bound": "hbm", "kernel": kname + " (FP32 SpMM in difference form fused with the p.q column dots)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_note": peak_note, "traffic": traffic, "algorithmic_bytes": bytes32,
-                "ms_per_launch": ms32}
+                "peak_note": peak_note, "traffic": traffic,
+                "traffic_note": cap["note"] if cap and traffic is not None else None,
+                "algorithmic_bytes": bytes32, "ms_per_launch": ms32, "solver_layout": sinfo}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -811,24 +889,22 @@ def main():
                "d2h_bytes_per_step": int(Lh.numel() * Lh.element_size())}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu and args.workload == "shell2mm":
+    if rank == 0 and world == 1 and not args.no_cpu:
+        text = cpu_pcg_text(args.workload)
         try:
-            cpu_s = oracle_once()
-            cpu = {"value": cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE_TEXT}
+            m = cpu_pcg_workload(args.workload, 1)
+            cpu = {"value": m["s_per_iteration"][0] * m["iterations"], "unit": UNIT, "cores": m["threads"],
+                   "kind": "oracle", "sample": text}
+            extra["cpu_pcg"] = dict(m, gpu_fp64_s_per_iteration=(
+                None if it64 is None else extra["fp64_lf_build_s"] / max(1, int(it64.max()))),
+                gpu_fp64_iterations=None if it64 is None else int(it64.max()))
         except Exception as ex:  # reported, never silently replaced
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %s" % ex}
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": "failed: %s" % ex}
         try:
-            c = cpu_pcg_once()
-            g = gpu_fp64_same_sample()
-            extra["cpu_pcg"] = {
-                "kind": "CPU block PCG, FP64, Jacobi, OpenMP (oracle/cpu_pcg.c)", "threads": c["threads"],
-                "sample": "transfer solve T = A^-1 B of the h=4 mm head (56235 nodes, 128 CEM electrodes), "
-                          "tol 1e-10",
-                "s": c["s"], "iterations": c["iterations"], "s_per_iteration": c["s"] / max(1, c["iterations"]),
-                "gpu_fp64_s": g["s"], "gpu_fp64_iterations": g["iterations"],
-                "gpu_fp64_s_per_iteration": g["s"] / max(1, g["iterations"])}
+            extra["cpu_oracle_direct"] = {"value": oracle_once(args.workload), "unit": UNIT, "cores": 1,
+                                          "kind": "oracle", "sample": DIRECT_SAMPLES[args.workload][1]}
         except Exception as ex:
-            extra["cpu_pcg"] = {"failed": str(ex)}
+            extra["cpu_oracle_direct"] = {"value": None, "sample": "failed: %s" % ex}
 
     if rank == 0:
         line = {"metric": METRIC, "value": sec_mixed, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -838,7 +914,9 @@ def main():
                 "config": {"workload": workload, "n_nodes": int(d["nodes"].shape[0]),
                            "n_tets": int(d["tets"].shape[0]), "electrodes": spec.n_electrodes,
                            "dipoles": spec.n_dipoles,
-                           "precision": "mixed", "l2": "inputs larger than L2 (T alone is 438 MB)",
+                           "precision": "mixed",
+                           "l2": "inputs larger than L2 (T alone is %.0f MB)" % (
+                               d["nodes"].shape[0] * spec.n_electrodes * 8 / 1e6),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "iterations_mixed_max": int(it_mixed.max()), "relres_mixed_max": float(rr_mixed.max()),
                 "iterations_fp64_max": None if it64 is None else int(it64.max()),
