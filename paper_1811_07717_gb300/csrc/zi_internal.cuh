@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "zi.h"
 
@@ -89,6 +90,31 @@ struct DevTmp {
     s = st;
     return dalloc_n(&p, n, st);
   }
+};
+
+// CUDA events that are destroyed on every exit path (timing helpers).
+struct EventSet {
+  std::vector<cudaEvent_t> ev;
+  EventSet() = default;
+  EventSet(const EventSet&) = delete;
+  EventSet& operator=(const EventSet&) = delete;
+  ~EventSet() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  // Creates k events; `flags` as for cudaEventCreateWithFlags.
+  cudaError_t create(size_t k, unsigned flags = cudaEventDefault) {
+    ev.assign(k, nullptr);
+    for (auto& e : ev) {
+      cudaError_t r = cudaEventCreateWithFlags(&e, flags);
+      if (r != cudaSuccess) {
+        e = nullptr;
+        return r;
+      }
+    }
+    return cudaSuccess;
+  }
+  cudaEvent_t operator[](size_t i) const { return ev[i]; }
 };
 
 // ---------------------------------------------------------------------------

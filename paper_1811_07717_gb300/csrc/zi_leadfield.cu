@@ -435,8 +435,8 @@ extern "C" int zi_time_source_apply(zi_system* S, const int32_t* F_nodes, const 
   ZI_CHECK(err.alloc(1, s));
   ZI_CHECK(flush.alloc(nflush, s));
   ZI_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-  std::vector<cudaEvent_t> ev(2 * reps);
-  for (auto& e : ev) ZI_CUDA(cudaEventCreate(&e));
+  EventSet ev;
+  ZI_CUDA(ev.create(2 * (size_t)reps));
   for (int r = 0; r < reps; ++r) {
     k_flush_l2<<<sm_count() * 8, 256, 0, s>>>(nflush, flush.p, (float)r);
     ZI_LAUNCH_CHECK();
@@ -451,7 +451,6 @@ extern "C" int zi_time_source_apply(zi_system* S, const int32_t* F_nodes, const 
     ZI_CUDA(cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]));
     tot += ms;
   }
-  for (auto& e : ev) cudaEventDestroy(e);
   int herr = 0;
   ZI_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   ZI_CUDA(cudaStreamSynchronize(s));
