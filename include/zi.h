@@ -152,6 +152,24 @@ int zi_mesh_from_surfaces(double h, int n_surf, const int64_t* tri_offset, const
 int zi_nearest_source(const double* points, int64_t n, const double* sources, int64_t P, int32_t* out,
                       cudaStream_t stream);
 
+/* Element of any tetrahedral mesh that holds each point (Sec. 2.5: source
+ * positions placed in the mesh): the element whose smallest barycentric
+ * coordinate at the point is largest, ties to the lowest element index; the
+ * point lies in the mesh when that coordinate is >= -1e-10.  Barycentric
+ * coordinates in FP64 from 3x3 determinants of vertex differences:
+ * D = det(x1-x0, x2-x0, x3-x0), l1 = det(x-x0, x2-x0, x3-x0)/D,
+ * l2 = det(x1-x0, x-x0, x3-x0)/D, l3 = det(x1-x0, x2-x0, x-x0)/D,
+ * l0 = 1 - l1 - l2 - l3.  Candidates come from a uniform grid of cells over
+ * the nodes' bounding box (each element listed in every cell its bounding box
+ * overlaps); the result does not depend on the order of those lists.
+ *   nodes: device n x 3 f64; tets: device m x 4 i32; pos: device P x 3 f64;
+ *   tet_out: device out, P i32 (-1 for a point outside the mesh).
+ * ZI_ERR_BAD_MESH if a point lies outside the mesh, ZI_ERR_NONFINITE for a
+ * non-finite coordinate, ZI_ERR_ARG for an element vertex outside the nodes.
+ * Synchronises. */
+int zi_locate_points(const double* nodes, int64_t n, const int32_t* tets, int64_t m,
+                     const double* pos, int64_t P, int32_t* tet_out, cudaStream_t stream);
+
 /* Element of a zi_mesh_from_grid mesh (same h, radii) that holds each point:
  * cube = floor(x/h) per axis, then the Kuhn tet whose axis order sorts the
  * fractional coordinates in descending order (first permutation on ties).
@@ -250,11 +268,49 @@ int zi_transfer(zi_system* sys, const zi_solver_opts* opts, double* T,
                 int32_t* iters, double* relres, cudaStream_t stream);
 
 /* Batched transfer: the systems of nb heads (any sizes, any electrode counts)
- * solved together in one persistent launch per iteration chunk, replayed as a
- * CUDA graph.  T[b] may be NULL.  Per-head iteration counts go to iters[b]
- * (host arrays of n_rhs each, may be NULL). */
+ * solved in the schedule of zi_batch_tune (tuned on the first call of a batch
+ * signature, cached after): the heads of its persistent set together in one
+ * persistent launch per iteration chunk, replayed as a CUDA graph, the others
+ * on their own iteration graphs.  T[b] may be NULL.  Per-head iteration counts
+ * go to iters[b] (host arrays of n_rhs each, may be NULL). */
 int zi_transfer_batched(zi_system* const* sys, int nb, const zi_solver_opts* opts,
                         double* const* T, int32_t* const* iters, cudaStream_t stream);
+
+/* The batch schedule chosen by the library's autotuner for zi_transfer_batched.
+ * Heads of the persistent set are solved together in one cooperative launch
+ * per chunk of 16 iterations (replayed from a CUDA graph); the others one after
+ * another on their own captured iteration graphs (zi_transfer's path).  The
+ * tuner ranks the heads by per-iteration work (nodes x padded right-hand
+ * sides) and times, from every head's initial state, a window of the solve
+ * (the first CG phase, at most 64 iterations): every head alone, and the
+ * persistent launch of the k smallest heads for k in {2, nb/4, nb/2, 3nb/4, nb};
+ * it keeps the k with the least estimated window time of the whole batch,
+ * t(k smallest together) + sum of the other heads' times alone (k = 0: every
+ * head alone).  The result is cached per batch signature (device, precision,
+ * preconditioner, each head's n, nnz and n_rhs in call order): only the first
+ * call of a signature pays for the timing.  Every head is reset to its
+ * initial state afterwards; T is untouched. */
+enum { ZI_BATCH_TUNED = 1, ZI_BATCH_CACHED = 2 };
+
+typedef struct zi_batch_schedule {
+  int32_t source;                         /* ZI_BATCH_TUNED (timed in this call) or ZI_BATCH_CACHED */
+  double est_window_ms;            /* estimated ms of the tuning window: the chosen schedule */
+  double est_window_ms_per_head;   /* every head alone */
+  double est_window_ms_persistent; /* every head in the persistent launch */
+} zi_batch_schedule;
+
+/* Runs (or looks up) the autotuner: persistent (host out, nb i32) gets 1 for the
+ * heads of the persistent launch.  info (host out) may be NULL.  Synchronises. */
+int zi_batch_tune(zi_system* const* sys, int nb, const zi_solver_opts* opts, int32_t* persistent,
+                  zi_batch_schedule* info, cudaStream_t stream);
+
+/* zi_transfer_batched with a given schedule: persistent (host in, nb i32) marks
+ * the heads of the persistent launch; chunk = iterations per launch (0: opts'
+ * check_every, else 25).  Results are bitwise reproducible for a fixed
+ * schedule. */
+int zi_transfer_batched_schedule(zi_system* const* sys, int nb, const zi_solver_opts* opts, double* const* T,
+                                 int32_t* const* iters, const int32_t* persistent, int chunk,
+                                 cudaStream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Lead field (App. A.2, Eq. aku)                                              */
@@ -271,6 +327,12 @@ int zi_transfer_batched(zi_system* const* sys, int nb, const zi_solver_opts* opt
  *   the handle holds no T.  Synchronises. */
 int zi_leadfield(zi_system* sys, const int32_t* dip_tet, int64_t P,
                  const zi_solver_opts* opts, double* L, cudaStream_t stream);
+
+/* The same lead field for dipoles given by position (device P x 3 f64): each
+ * is placed in its element of the system's own mesh by zi_locate_points, then
+ * as zi_leadfield.  ZI_ERR_BAD_MESH if a dipole lies outside the mesh. */
+int zi_leadfield_at(zi_system* sys, const double* dip_pos, int64_t P,
+                    const zi_solver_opts* opts, double* L, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* H(div) sources (Sec. 2.1, primary current model)                            */
@@ -397,7 +459,11 @@ int zi_eit_jacobian(zi_system* sys, const double* I, int np, int mode,
  * and code that must not allocate inside a latency-critical loop.  It calls no
  * cudaMalloc, cudaFree or allocating routine; its scratch is one fixed array in
  * the library's device memory (ZI_NOALLOC_SCRATCH_BYTES on every GPU that
- * loads the library, held until the process exits).
+ * loads the library, held until the process exits).  Its device address is
+ * looked up once per device and kept for the life of the process: this
+ * assumes the device's primary context lives as long as the process (after a
+ * cudaDeviceReset, or a context destroyed and created again, the kept address
+ * is stale; do not call this entry point after either).
  *   The system must already hold T (zi_transfer has run; otherwise ZI_ERR_ARG,
  *   since solving would allocate).  dip_tet: device P i32; L: device out,
  *   n_rows_L x 3P f64, as in zi_leadfield.
@@ -461,6 +527,61 @@ int zi_time_spmm(zi_system* sys, int precision, int reps, double* ms_per_launch,
  * H^T (ncols x n_rhs f64). */
 int zi_time_source_apply(zi_system* sys, const int32_t* F_nodes, const double* F_w, int64_t ncols, int K,
                          int reps, double* ms_per_launch, double* bytes_per_launch, cudaStream_t stream);
+
+/* Applies the solver's own sparse operator, with the same kernel and the same
+ * fused column reduction that every CG iteration runs (Sec. 2.3.1, the
+ * product of A (App. A.1) with the search directions of all right-hand sides):
+ *   opts->precision == ZI_FP64: Y = S A~ S X, the FP64 CG's operator: A~ is A
+ *     without its rounding-noise entries (|a_ij| <= 2^-40 sqrt(|a_ii a_jj|)),
+ *     S = D^-1/2 with D the diagonal of opts->precond (a_ii for Jacobi,
+ *     sum_j |a_ij| for LDP);
+ *   ZI_MIXED: Y = A X by the inner FP32 operator: X rounded to FP32, A in
+ *     difference form (A x)_i = c_i x_i + sum_{j != i} a_ij (x_j - x_i) with
+ *     c_i the FP64 row sum, entries below 2^-24 of the scaled diagonal left to
+ *     c_i; FP32 arithmetic.
+ *   X: device n x n_rhs f64 (node-major, like T); Y: device out, n x n_rhs f64.
+ *   dots: device out, n_rhs f64, or NULL: the column dots sum_i x_ic y_ic as the
+ *     CG forms its p.q (per-thread partials, then per-block and per-cluster
+ *     sums in a fixed order).
+ * Builds the solver's matrix copies when needed and overwrites the solver's
+ * work vectors (the next zi_transfer starts afresh); T is kept.  A diagnostic:
+ * it lets a test check the operator and its reduction row by row.
+ * Synchronises. */
+int zi_apply_operator(zi_system* sys, const zi_solver_opts* opts, const double* X, double* Y, double* dots,
+                      cudaStream_t stream);
+
+/* Layout of the FP32 sparse product (zi_solver_info.spmm32). */
+enum {
+  ZI_SPMM32_NONE = 0,          /* the FP32 copy has not been built yet */
+  ZI_SPMM32_ELL = 1,           /* 8 slots per row, longer rows continue in a CSR tail */
+  ZI_SPMM32_ELL_OVERFLOW = 2   /* as 1, with eight more slots per row staged with the row (many long rows) */
+};
+
+typedef struct zi_solver_info {
+  int32_t ld;                   /* columns of the solver's vectors (n_rhs padded) */
+  int32_t threads_per_row64;    /* FP64 kernels: threads per row, 16-byte vectors per thread */
+  int32_t vectors_per_thread64;
+  int32_t threads_per_row32;    /* FP32 kernels */
+  int32_t vectors_per_thread32;
+  int32_t spmm32;               /* ZI_SPMM32_* */
+  int64_t nnz64;                /* entries of the FP64 solver copy (0 until built) */
+  int64_t nnz32;                /* entries of the FP32 copy (0 until built) */
+  int64_t tail_rows;            /* rows of the FP32 copy with more than 8 entries */
+  int64_t tail_entries;         /* entries beyond the first 8 of those rows */
+  int32_t ell_tiled;            /* 1: the FP32 copy stores its rows in tile columns (nodes on a grid), 0: in
+                                   row order; the product is the same either way */
+} zi_solver_info;
+
+/* The solver's layout for this system: vector width and row split, and the
+ * sizes and FP32 product layout of the matrix copies built by the last
+ * zi_transfer or zi_apply_operator.  Host only; never synchronises. */
+int zi_solver_get_info(const zi_system* sys, zi_solver_info* info);
+
+/* Device memory of the library's private pool on the current device (every
+ * library allocation comes from it): bytes in use now and the high-water mark
+ * since the last reset (reset_high != 0 sets the mark to zero after reading).
+ * A diagnostic: a test reads it around calls that must not allocate. */
+int zi_memory_stats(int64_t* used_now, int64_t* used_high, int reset_high);
 
 /* Number of libzi kernels launched by this process so far (graph replays
  * count each kernel node). */

@@ -72,7 +72,7 @@ cudaMemPool_t g_pools[64];
 bool g_pool_init[64];
 }  // namespace
 
-static int get_pool(cudaMemPool_t* out) {
+int get_pool(cudaMemPool_t* out) {
   int dev = 0;
   ZI_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return set_error(ZI_ERR_ARG, "device ordinal %d out of range", dev);
@@ -251,6 +251,21 @@ extern "C" {
 int zi_version(void) { return 10000; }
 
 int64_t zi_kernel_launches(void) { return zi::launches_total(); }
+
+int zi_memory_stats(int64_t* used_now, int64_t* used_high, int reset_high) {
+  cudaMemPool_t pool = nullptr;
+  ZI_CHECK(zi::get_pool(&pool));
+  uint64_t cur = 0, high = 0;
+  ZI_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &cur));
+  ZI_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high));
+  if (used_now) *used_now = (int64_t)cur;
+  if (used_high) *used_high = (int64_t)high;
+  if (reset_high) {
+    uint64_t zero = 0;
+    ZI_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+  }
+  return ZI_OK;
+}
 
 int zi_last_error(char* buf, size_t len) {
   if (buf && len) {

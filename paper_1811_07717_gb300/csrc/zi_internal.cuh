@@ -71,6 +71,7 @@ int device_error_to_status(int dev_err);
 
 int dalloc(void** p, size_t bytes, cudaStream_t s);
 void dfree(void* p, cudaStream_t s);
+int get_pool(cudaMemPool_t* out);  // the library's pool of the current device
 
 template <typename T>
 int dalloc_n(T** p, size_t n, cudaStream_t s) {

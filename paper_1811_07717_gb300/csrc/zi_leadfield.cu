@@ -492,7 +492,9 @@ std::mutex g_noalloc_mu;
 void* g_noalloc_addr[64];
 
 // Device address of the scratch on the current device, looked up once per
-// device with that device current.
+// device with that device current and kept for the life of the process: the
+// cache assumes one primary context per device for the whole process (a
+// cudaDeviceReset or a re-created context would leave a stale address).
 int noalloc_scratch(void** out) {
   int dev = 0;
   ZI_CUDA(cudaGetDevice(&dev));

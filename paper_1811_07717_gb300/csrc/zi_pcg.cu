@@ -24,6 +24,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -427,12 +430,12 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
     if (g < rpb) {
       for (int k = 0; k < slots; ++k) {
         const int lr = g + k * rpb;
-        const int i = (int)(base + lr);
         if (base + lr >= n) break;
         const int4 c0 = bc[2 * lr], c1 = bc[2 * lr + 1];
         int j[ELL_K] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
         const bool tail = j[0] < 0;
         j[0] = tail ? ~j[0] : j[0];
+        const int i = j[0];  // the row: slot 0 is its diagonal (the copy may store rows in a tiled order)
         V x[ELL_K][CPTV];
 #pragma unroll
         for (int u = 0; u < ELL_K; ++u)
@@ -842,26 +845,29 @@ __global__ void k_tail_count(int64_t n, const int32_t* __restrict__ rowptr32, in
 // row's own slots; built when many rows have a tail (anisotropic elements
 // couple all 14 Kuhn neighbours).
 __global__ void k_fill_ovf(int64_t n, const int32_t* __restrict__ tail_ptr, const int32_t* __restrict__ tail_ci,
-                           const float* __restrict__ tail_va, int32_t* __restrict__ oci, float* __restrict__ ova) {
+                           const float* __restrict__ tail_va, const int32_t* __restrict__ pos,
+                           int32_t* __restrict__ oci, float* __restrict__ ova) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int t0 = tail_ptr[i], t1 = tail_ptr[i + 1];
+    const int64_t r = pos ? pos[i] : i;
     for (int u = 0; u < ELL_K; ++u) {
       const bool in = t0 + u < t1;
-      oci[i * ELL_K + u] = in ? tail_ci[t0 + u] : -1;
-      ova[i * ELL_K + u] = in ? tail_va[t0 + u] : 0.f;
+      oci[r * ELL_K + u] = in ? tail_ci[t0 + u] : -1;
+      ova[r * ELL_K + u] = in ? tail_va[t0 + u] : 0.f;
     }
   }
 }
 
 __global__ void k_fill_ell(int64_t n, const int32_t* __restrict__ rowptr32, const int32_t* __restrict__ colind32,
-                           const float* __restrict__ v32, int32_t* __restrict__ ci, float* __restrict__ va,
-                           const int32_t* __restrict__ tail_ptr, int32_t* __restrict__ tail_ci,
+                           const float* __restrict__ v32, const int32_t* __restrict__ pos, int32_t* __restrict__ ci,
+                           float* __restrict__ va, const int32_t* __restrict__ tail_ptr, int32_t* __restrict__ tail_ci,
                            float* __restrict__ tail_va) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int o = 1;
     int t = tail_ptr ? tail_ptr[i] : 0;
-    int32_t* cr = ci + i * ELL_K;
-    float* vr = va + i * ELL_K;
+    const int64_t r = pos ? pos[i] : i;  // storage position of row i
+    int32_t* cr = ci + r * ELL_K;
+    float* vr = va + r * ELL_K;
     cr[0] = (int32_t)i;
     vr[0] = 0.f;
     for (int k = rowptr32[i]; k < rowptr32[i + 1]; ++k) {
@@ -883,6 +889,83 @@ __global__ void k_fill_ell(int64_t n, const int32_t* __restrict__ rowptr32, cons
     }
     if (tail_ptr && tail_ptr[i + 1] > tail_ptr[i]) cr[0] = ~(int32_t)i;
   }
+}
+
+// Storage order of the FP32 ELL copy.  The mesh numbers its nodes
+// lexicographically over the grid (x slowest, z fastest), so a node's x
+// neighbours are about G^2 rows away, and the SpMM's sweep needs a window of
+// P far larger than L2 on a 1 mm head (P rows were read from HBM about 2.7
+// times per launch).  When the nodes lie on a regular grid, the copy stores
+// the rows in tile columns: tiles of ORD_TX x ORD_TY nodes in (x, y), each
+// column streamed along z, nodes of a z-layer of the tile in (x, y) order.
+// In-tile neighbours are then at most ORD_TX * ORD_TY rows apart, y-tile
+// neighbours one tile column apart, and only the x-faces of the tiles (2 rows
+// in ORD_TX) reach further.  The vectors stay in mesh order; the SpMM takes
+// each row's index from its slot 0.
+constexpr int ORD_TX = 16, ORD_TY = 8;
+
+__device__ __forceinline__ unsigned long long ord_key(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+inline double ord_key_inv(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  double v;
+  memcpy(&v, &b, sizeof(v));
+  return v;
+}
+
+// keys[0..2]: min coordinate per axis; keys[3]: smallest positive edge extent
+// (the largest |component| of an edge vector: h on a Kuhn grid).
+__global__ void k_ord_extent(int64_t n, const double* __restrict__ nodes, int64_t m, const int32_t* __restrict__ tets,
+                             unsigned long long* __restrict__ keys) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+    for (int d = 0; d < 3; ++d) atomicMin(keys + d, ord_key(nodes[3 * i + d]));
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride) {
+    const int32_t a = tets[4 * e], b = tets[4 * e + 1];
+    double ext = 0.0;
+    for (int d = 0; d < 3; ++d) ext = fmax(ext, fabs(nodes[3 * (int64_t)a + d] - nodes[3 * (int64_t)b + d]));
+    if (ext > 0.0) atomicMin(keys + 3, ord_key(ext));
+  }
+}
+
+// Grid coordinates of every node; *bad = 1 if a node is off the grid.
+__global__ void k_ord_coords(int64_t n, const double* __restrict__ nodes, double lx, double ly, double lz, double h,
+                             int32_t* __restrict__ q, int* __restrict__ dims, int* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double lo[3] = {lx, ly, lz};
+    for (int d = 0; d < 3; ++d) {
+      const double f = (nodes[3 * i + d] - lo[d]) / h;
+      const double r = rint(f);
+      if (!(fabs(f - r) <= 1e-6) || r < 0.0 || r > 1e6) {
+        atomicExch(bad, 1);
+        q[3 * i + d] = 0;
+        continue;
+      }
+      q[3 * i + d] = (int32_t)r;
+      atomicMax(dims + d, (int)r + 1);
+    }
+  }
+}
+
+__device__ __forceinline__ int64_t ord_cell(const int32_t* q, int ny, int nz) {
+  const int x = q[0], y = q[1], z = q[2];
+  const int64_t ty = (ny + ORD_TY - 1) / ORD_TY;
+  const int64_t col = (int64_t)(x / ORD_TX) * ty + y / ORD_TY;
+  return ((col * nz + z) * ORD_TX + x % ORD_TX) * ORD_TY + y % ORD_TY;
+}
+
+__global__ void k_ord_mark(int64_t n, const int32_t* __restrict__ q, int ny, int nz, int32_t* __restrict__ occ,
+                           int* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (atomicAdd(occ + ord_cell(q + 3 * i, ny, nz), 1) != 0) atomicExch(bad, 1);  // two nodes in one cell
+}
+
+__global__ void k_ord_pos(int64_t n, const int32_t* __restrict__ q, int ny, int nz, const int32_t* __restrict__ cpos,
+                          int32_t* __restrict__ pos) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    pos[i] = cpos[ord_cell(q + 3 * i, ny, nz)];
 }
 
 // Builds the padded, scaled right-hand side r~ = S b (n x ld) and the column
@@ -1103,6 +1186,8 @@ struct SolverScratch {
   int32_t* ovf_ci = nullptr;    // n x ELL_K overflow slots (null unless many rows have a tail)
   float* ovf_va = nullptr;
   int64_t ntail = 0;
+  int64_t tail_rows = 0;        // rows of the FP32 copy with more than ELL_K entries
+  bool ell_tiled = false;       // the ELL copy stores its rows in the tiled order
   int32_t* tail_ci = nullptr;
   float* tail_va = nullptr;
   // FP64 vectors n x ld
@@ -1610,6 +1695,63 @@ struct HeadRun {
 
 int mixed_phase_begin(HeadRun& h);
 
+// Storage position of every row of the FP32 ELL copy in the tiled order (see
+// ORD_TX), or pos left empty (row order): when the nodes are not on a grid, or
+// when the row order's reach already fits L2 comfortably -- two x-layers of
+// P rows (about 2 n / nx rows of ld floats) within 32 MB, as on the 2 mm head.
+// ZI_ELL_ORDER=rows or =tiles in the environment forces either order (tests).
+static int ell_order(zi_system* S, int ld, cudaStream_t st, DevTmp<int32_t>& pos, bool* tiled) {
+  *tiled = false;
+  const int64_t n = S->n, m = S->m;
+  if (n < 1 || m < 1) return ZI_OK;
+  const char* force = getenv("ZI_ELL_ORDER");
+  const bool want_rows = force && !strcmp(force, "rows"), want_tiles = force && !strcmp(force, "tiles");
+  if (want_rows) return ZI_OK;
+  DevTmp<unsigned long long> keys;
+  ZI_CHECK(keys.alloc(4, st));
+  ZI_CUDA(cudaMemsetAsync(keys.p, 0xff, 4 * sizeof(unsigned long long), st));
+  k_ord_extent<<<grid_for(std::max(n, m), 256), 256, 0, st>>>(n, S->nodes, m, S->tets, keys.p);
+  ZI_LAUNCH_CHECK();
+  unsigned long long hk[4];
+  ZI_CUDA(cudaMemcpyAsync(hk, keys.p, sizeof(hk), cudaMemcpyDeviceToHost, st));
+  ZI_CUDA(cudaStreamSynchronize(st));
+  const double h = ord_key_inv(hk[3]);
+  if (!(h > 0.0) || !isfinite(h)) return ZI_OK;
+  DevTmp<int32_t> q;
+  DevTmp<int> db;  // dims[3], bad
+  ZI_CHECK(q.alloc(3 * n, st));
+  ZI_CHECK(db.alloc(4, st));
+  ZI_CUDA(cudaMemsetAsync(db.p, 0, 4 * sizeof(int), st));
+  k_ord_coords<<<grid_for(n, 256), 256, 0, st>>>(n, S->nodes, ord_key_inv(hk[0]), ord_key_inv(hk[1]),
+                                                 ord_key_inv(hk[2]), h, q.p, db.p, db.p + 3);
+  ZI_LAUNCH_CHECK();
+  int hd[4];
+  ZI_CUDA(cudaMemcpyAsync(hd, db.p, sizeof(hd), cudaMemcpyDeviceToHost, st));
+  ZI_CUDA(cudaStreamSynchronize(st));
+  if (hd[3]) return ZI_OK;
+  if (!want_tiles && 2.0 * (double)n / hd[0] * ld * sizeof(float) <= 32e6) return ZI_OK;
+  const int64_t ntx = (hd[0] + ORD_TX - 1) / ORD_TX, nty = (hd[1] + ORD_TY - 1) / ORD_TY;
+  const int64_t cells = ntx * nty * (int64_t)hd[2] * ORD_TX * ORD_TY;
+  if (cells > ((int64_t)1 << 28) || cells > 64 * n) return ZI_OK;  // a sparse grid: keep row order
+  DevTmp<int32_t> occ, cpos;
+  ZI_CHECK(occ.alloc(cells, st));
+  ZI_CHECK(cpos.alloc(cells + 1, st));
+  ZI_CUDA(cudaMemsetAsync(occ.p, 0, sizeof(int32_t) * cells, st));
+  k_ord_mark<<<grid_for(n, 256), 256, 0, st>>>(n, q.p, hd[1], hd[2], occ.p, db.p + 3);
+  ZI_LAUNCH_CHECK();
+  ZI_CUDA(cudaMemcpyAsync(hd + 3, db.p + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ZI_CUDA(cudaStreamSynchronize(st));
+  if (hd[3]) return ZI_OK;
+  int64_t total = 0;
+  ZI_CHECK(exclusive_scan_i32(occ.p, cpos.p, cells, &total, st));
+  if (total != n) return ZI_OK;
+  ZI_CHECK(pos.alloc(n, st));
+  k_ord_pos<<<grid_for(n, 256), 256, 0, st>>>(n, q.p, hd[1], hd[2], cpos.p, pos.p);
+  ZI_LAUNCH_CHECK();
+  *tiled = true;
+  return ZI_OK;
+}
+
 // Scaled FP64 matrix, and the FP32 CSR / ELL copies for the mixed path.
 static int prepare_matrices(zi_system* S, const zi_solver_opts* o, cudaStream_t st) {
   SolverScratch* w = S->solver;
@@ -1680,9 +1822,13 @@ static int prepare_matrices(zi_system* S, const zi_solver_opts* o, cudaStream_t 
       w->graph32 = nullptr;
       w->graph_chunk32 = 0;
     }
-    k_fill_ell<<<grid_for(n, 256), 256, 0, st>>>(n, w->rowptr32, w->colind32, w->v32, w->ell_ci, w->ell_va,
+    DevTmp<int32_t> pos;
+    bool tiled = false;
+    ZI_CHECK(ell_order(S, w->ld, st, pos, &tiled));
+    k_fill_ell<<<grid_for(n, 256), 256, 0, st>>>(n, w->rowptr32, w->colind32, w->v32, pos.p, w->ell_ci, w->ell_va,
                                                  w->tail_ptr, w->tail_ci, w->tail_va);
     ZI_LAUNCH_CHECK();
+    w->ell_tiled = tiled;
     // overflow slots when more than 5 % of the rows have a tail
     int h_ntrows = 0;
     ZI_CUDA(cudaMemcpyAsync(&h_ntrows, ntrows.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1694,10 +1840,12 @@ static int prepare_matrices(zi_system* S, const zi_solver_opts* o, cudaStream_t 
     if (ntail > 0 && (int64_t)h_ntrows * 20 > n) {
       ZI_CHECK(dalloc_n(&w->ovf_ci, (size_t)n * ELL_K, st));
       ZI_CHECK(dalloc_n(&w->ovf_va, (size_t)n * ELL_K, st));
-      k_fill_ovf<<<grid_for(n, 256), 256, 0, st>>>(n, w->tail_ptr, w->tail_ci, w->tail_va, w->ovf_ci, w->ovf_va);
+      k_fill_ovf<<<grid_for(n, 256), 256, 0, st>>>(n, w->tail_ptr, w->tail_ci, w->tail_va, pos.p, w->ovf_ci,
+                                                   w->ovf_va);
       ZI_LAUNCH_CHECK();
     }
     w->ntail = ntail;
+    w->tail_rows = h_ntrows;
     w->v32_ready = true;
   }
   return ZI_OK;
@@ -1900,14 +2048,31 @@ int head_finish(HeadRun& h, double* Tout, int32_t* iters, double* relres) {
   return ZI_OK;
 }
 
+// CG iterations of one head's current phase on its own stream (graph
+// replays of `chunk` iterations) until it stops or `maxit` ran.
+static int run_inner(HeadRun& h, int maxit, int chunk, int* ran) {
+  SolverScratch* w = h.S->solver;
+  if (h.mixed) {
+    double* dtrue_saved = w->dtrue;
+    w->dtrue = w->w32;
+    int st2 = run_cg<float>(h.p32, w, w->v32, w->x32, w->r32, w->p32, w->q32, maxit, chunk, &w->graph32,
+                            &w->graph_chunk32, ran);
+    w->dtrue = dtrue_saved;
+    return st2;
+  }
+  return run_cg<double>(h.p64, w, w->v64, w->X, w->R, w->P, w->Q, maxit, chunk, &w->graph64, &w->graph_chunk64,
+                        ran);
+}
+
 int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* iters, double* relres,
                   cudaStream_t user) {
   ZI_CHECK(ensure_scratch(S, o, user));
   SolverScratch* w = S->solver;
   cudaStream_t st = w->stream;
   // order the internal stream after the caller's stream
-  cudaEvent_t ev;
-  ZI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  EventSet evs;
+  ZI_CUDA(evs.create(1, cudaEventDisableTiming));
+  cudaEvent_t ev = evs[0];
   ZI_CUDA(cudaEventRecord(ev, user));
   ZI_CUDA(cudaStreamWaitEvent(st, ev, 0));
   HeadRun h;
@@ -1918,24 +2083,13 @@ int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* 
   const int chunk = o->check_every > 0 ? o->check_every : 25;
   while (!h.done) {
     int ran = 0;
-    if (h.mixed) {
-      double* dtrue_saved = w->dtrue;
-      w->dtrue = w->w32;
-      int st2 = run_cg<float>(h.p32, w, w->v32, w->x32, w->r32, w->p32, w->q32, o->maxit - h.total, chunk,
-                              &w->graph32, &w->graph_chunk32, &ran);
-      w->dtrue = dtrue_saved;
-      ZI_CHECK(st2);
-    } else {
-      ZI_CHECK(run_cg<double>(h.p64, w, w->v64, w->X, w->R, w->P, w->Q, o->maxit - h.total, chunk, &w->graph64,
-                              &w->graph_chunk64, &ran));
-    }
+    ZI_CHECK(run_inner(h, o->maxit - h.total, chunk, &ran));
     ZI_CHECK(head_after_inner(h, ran));
   }
   ZI_CHECK(head_finish(h, Tout, iters, relres));
   ZI_CUDA(cudaEventRecord(ev, st));
   ZI_CUDA(cudaStreamWaitEvent(user, ev, 0));
   ZI_CUDA(cudaStreamSynchronize(st));
-  cudaEventDestroy(ev);
   return h.status;
 }
 
@@ -2161,12 +2315,13 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
             vfma(acc, a[0], x[0]);
 #pragma unroll
             for (int u = 1; u < ELL_K; ++u) vfma_diff(acc, a[u], x[u], x[0]);
+            // the row is slot 0's column (the ELL copy may store rows in a tiled order)
             if (tail) {
-              const int t0 = __ldg(H.tail_ptr + i), t1 = __ldg(H.tail_ptr + i + 1);
+              const int t0 = __ldg(H.tail_ptr + j[0]), t1 = __ldg(H.tail_ptr + j[0] + 1);
               for (int t = t0; t < t1; ++t)
                 vfma_diff(acc, __ldg(H.tail_va + t), ldg_v(Pc + __ldg(H.tail_ci + t) * nv), x[0]);
             }
-            Qc[i * nv] = acc;
+            Qc[j[0] * nv] = acc;
 #pragma unroll
             for (int kk = 0; kk < W; ++kk) acc_pq[0][kk] += vget(x[0], kk) * vget(acc, kk);
             i = inext;
@@ -2503,14 +2658,28 @@ static int run_batched_chunk(std::vector<HeadRun*>& act, int chunk, cudaStream_t
   return ZI_OK;
 }
 
+// Heads' scratch of the persistent launch: barrier words and group sums.
+static int batch_prepare(zi_system* S, const zi_solver_opts* o, cudaStream_t st) {
+  ZI_CHECK(ensure_scratch(S, o, st));
+  SolverScratch* w = S->solver;
+  if (!w->bar) ZI_CHECK(dalloc_n(&w->bar, 2 + batch_groups(w->nblk), st));
+  if (!w->gpart) ZI_CHECK(dalloc_n(&w->gpart, 3 * (size_t)batch_groups(w->nblk) * w->ld, st));
+  return ZI_OK;
+}
+
 int transfer_batched_impl(zi_system* const* sys, int nb, const zi_solver_opts* o, double* const* Tout,
-                          int32_t* const* iters, cudaStream_t user) {
+                          int32_t* const* iters, cudaStream_t user, int chunk_req = 0) {
+  EventSet evs;
+  ZI_CUDA(evs.create(1, cudaEventDisableTiming));
+  cudaEvent_t ev = evs[0];
   cudaStream_t st;
   ZI_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-  cudaEvent_t ev;
-  ZI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-  ZI_CUDA(cudaEventRecord(ev, user));
-  ZI_CUDA(cudaStreamWaitEvent(st, ev, 0));
+  cudaError_t e0 = cudaEventRecord(ev, user);
+  if (e0 == cudaSuccess) e0 = cudaStreamWaitEvent(st, ev, 0);
+  if (e0 != cudaSuccess) {
+    cudaStreamDestroy(st);
+    return cuda_error(e0, "ordering the batch stream after the caller's", __FILE__, __LINE__);
+  }
   std::vector<HeadRun> heads(nb);
   int status = ZI_OK;
   auto run = [&]() -> int {
@@ -2522,13 +2691,10 @@ int transfer_batched_impl(zi_system* const* sys, int nb, const zi_solver_opts* o
       heads[b].S = sys[b];
       heads[b].o = o;
       heads[b].st = st;
-      ZI_CHECK(ensure_scratch(sys[b], o, st));
-      SolverScratch* w = sys[b]->solver;
-      if (!w->bar) ZI_CHECK(dalloc_n(&w->bar, 2 + batch_groups(w->nblk), st));
-      if (!w->gpart) ZI_CHECK(dalloc_n(&w->gpart, 3 * (size_t)batch_groups(w->nblk) * w->ld, st));
+      ZI_CHECK(batch_prepare(sys[b], o, st));
       ZI_CHECK(head_begin(heads[b]));
     }
-    const int chunk = o->check_every > 0 ? o->check_every : 25;
+    const int chunk = chunk_req > 0 ? chunk_req : (o->check_every > 0 ? o->check_every : 25);
     const bool mixed = o->precision == ZI_MIXED;
     for (;;) {
       std::vector<HeadRun*> act;
@@ -2561,7 +2727,6 @@ int transfer_batched_impl(zi_system* const* sys, int nb, const zi_solver_opts* o
   cudaEventRecord(ev, st);
   cudaStreamWaitEvent(user, ev, 0);
   cudaStreamSynchronize(st);
-  cudaEventDestroy(ev);
   cudaStreamDestroy(st);
   return rs != ZI_OK ? rs : status;
 }
@@ -2594,6 +2759,258 @@ int zi::check_opts(const zi_solver_opts* o) {
   return ZI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batch schedule autotuner.  A batch runs its heads in two ways: the heads of
+// the persistent set together in the cooperative launch (k_cg_batched), the
+// others one after another on their own captured iteration graphs (the
+// per-head path, whose FP32 SpMM stages its slots by TMA).  Small heads leave
+// most of the GPU idle on their own and gain from sharing it; a head that fills
+// the GPU gains nothing there and pays the persistent kernel's barriers and
+// the idle blocks of heads whose refinement phase has ended inside a chunk.
+// The tuner ranks the heads by per-iteration work (n x ld) and times, from
+// every head's initial state, a window of the solve -- the first CG phase,
+// capped at TUNE_WINDOW iterations -- in two ways:
+//   c_h    -- head h alone on the per-head path;
+//   t(S_k) -- the persistent launch of the k smallest heads (chunks of
+//             PERSISTENT_CHUNK iterations), k in {2, nb/4, nb/2, 3nb/4, nb};
+// and keeps the k with the least estimated time of the window,
+// E(k) = t(S_k) + sum_{h not in S_k} c_h  (E(0): every head alone).  The winner
+// is cached per batch signature (device, precision, preconditioner and each
+// head's n, nnz and n_rhs in call order), so only the first call of a class
+// pays for the timing.  Every head is reset to its initial state afterwards.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int TUNE_CHUNK = 16;
+constexpr int TUNE_WINDOW = 64;
+constexpr int PERSISTENT_CHUNK = 16;  // iterations per launch of the persistent kernel in tuned schedules
+
+struct TuneEntry {
+  std::vector<int32_t> persistent;
+  double est_plan = 0.0, est_per_head = 0.0, est_persistent = 0.0;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneEntry> g_tune;
+
+std::string batch_key(zi_system* const* sys, int nb, const zi_solver_opts* o) {
+  int dev = 0;
+  (void)cudaGetDevice(&dev);
+  std::string k = std::to_string(dev) + "/" + std::to_string(o->precision) + "/" + std::to_string(o->precond);
+  for (int b = 0; b < nb; ++b)
+    k += "|" + std::to_string(sys[b]->n) + ":" + std::to_string(sys[b]->nnz) + ":" + std::to_string(sys[b]->n_rhs);
+  return k;
+}
+
+// ms of the tuning window of head S alone on the per-head path (its graph is
+// captured first, outside the timed window).
+int time_per_head(zi_system* S, const zi_solver_opts* o, cudaStream_t user, double* ms) {
+  ZI_CHECK(ensure_scratch(S, o, user));
+  ZI_CUDA(cudaStreamSynchronize(user));  // the solver stream uses what was allocated on the caller's
+  HeadRun h;
+  h.S = S;
+  h.o = o;
+  h.st = S->solver->stream;
+  int ran = 0;
+  ZI_CHECK(head_begin(h));
+  ZI_CHECK(run_inner(h, TUNE_CHUNK, TUNE_CHUNK, &ran));  // captures the graph
+  ZI_CHECK(head_begin(h));
+  EventSet ev;
+  ZI_CUDA(ev.create(2));
+  ZI_CUDA(cudaEventRecord(ev[0], h.st));
+  ZI_CHECK(run_inner(h, TUNE_WINDOW, TUNE_CHUNK, &ran));
+  ZI_CUDA(cudaEventRecord(ev[1], h.st));
+  ZI_CUDA(cudaStreamSynchronize(h.st));
+  float t = 0.f;
+  ZI_CUDA(cudaEventElapsedTime(&t, ev[0], ev[1]));
+  *ms = t;
+  return ZI_OK;
+}
+
+// ms of the tuning window of the heads `set` in the persistent launch.
+template <typename T>
+int time_persistent(const std::vector<zi_system*>& set, const zi_solver_opts* o, cudaStream_t st, double* ms) {
+  const bool mixed = o->precision == ZI_MIXED;
+  std::vector<HeadRun> heads(set.size());
+  for (size_t b = 0; b < set.size(); ++b) {
+    heads[b].S = set[b];
+    heads[b].o = o;
+    heads[b].st = st;
+    ZI_CHECK(batch_prepare(set[b], o, st));
+    ZI_CHECK(head_begin(heads[b]));
+  }
+  DevTmp<int> d_err;
+  ZI_CHECK(d_err.alloc(1, st));
+  ZI_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int), st));
+  BatchCtx ctx(st);
+  std::vector<HeadRun*> act;
+  for (auto& h : heads) act.push_back(&h);
+  ZI_CHECK(run_batched_chunk<T>(act, TUNE_CHUNK, st, d_err.p, ctx));  // captures the graph
+  for (auto& h : heads) ZI_CHECK(head_begin(h));
+  std::vector<bool> fin(heads.size(), false);
+  EventSet ev;
+  ZI_CUDA(ev.create(2));
+  ZI_CUDA(cudaEventRecord(ev[0], st));
+  for (;;) {
+    act.clear();
+    for (size_t b = 0; b < heads.size(); ++b)
+      if (!fin[b]) act.push_back(&heads[b]);
+    if (act.empty()) break;
+    ZI_CHECK(run_batched_chunk<T>(act, TUNE_CHUNK, st, d_err.p, ctx));
+    int herr = 0;
+    ZI_CUDA(cudaMemcpyAsync(&herr, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ZI_CUDA(cudaStreamSynchronize(st));
+    ZI_CHECK(device_error_to_status(herr));
+    for (size_t b = 0; b < heads.size(); ++b) {
+      if (fin[b]) continue;
+      int c3[3];
+      ZI_CUDA(cudaMemcpyAsync(c3, set[b]->solver->cnt, sizeof(c3), cudaMemcpyDeviceToHost, st));
+      ZI_CUDA(cudaStreamSynchronize(st));
+      fin[b] = c3[0] == 0 || (mixed && c3[2] > 0) || c3[1] >= TUNE_WINDOW;
+    }
+  }
+  ZI_CUDA(cudaEventRecord(ev[1], st));
+  ZI_CUDA(cudaStreamSynchronize(st));
+  float t = 0.f;
+  ZI_CUDA(cudaEventElapsedTime(&t, ev[0], ev[1]));
+  *ms = t;
+  return ZI_OK;
+}
+
+int batch_tune(zi_system* const* sys, int nb, const zi_solver_opts* o, int32_t* persistent, zi_batch_schedule* info,
+               cudaStream_t user) {
+  const std::string key = batch_key(sys, nb, o);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      std::copy(it->second.persistent.begin(), it->second.persistent.end(), persistent);
+      if (info) {
+        info->source = ZI_BATCH_CACHED;
+        info->est_window_ms = it->second.est_plan;
+        info->est_window_ms_per_head = it->second.est_per_head;
+        info->est_window_ms_persistent = it->second.est_persistent;
+      }
+      return ZI_OK;
+    }
+  }
+  TuneEntry e;
+  e.persistent.assign(nb, 0);
+  if (nb >= 2) {
+    ZI_CUDA(cudaStreamSynchronize(user));
+    std::vector<int> order(nb);
+    for (int b = 0; b < nb; ++b) order[b] = b;
+    auto work = [&](int b) {
+      int ld, c64, c32;
+      choose_layout(sys[b]->n_rhs, &ld, &c64, &c32);
+      return (double)sys[b]->n * ld;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) < work(b); });
+    std::vector<double> c(nb);
+    for (int b = 0; b < nb; ++b) ZI_CHECK(time_per_head(sys[b], o, user, &c[b]));
+    double all_alone = 0.0;
+    for (double x : c) all_alone += x;
+    int best_k = 0;
+    double best = all_alone, t_all = 0.0;
+    cudaStream_t st;
+    ZI_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    int rs = ZI_OK;
+    std::vector<int> ks;
+    for (int k : {2, (nb + 3) / 4, (nb + 1) / 2, (3 * nb + 3) / 4, nb})
+      if (k >= 2 && k <= nb && (ks.empty() || k > ks.back())) ks.push_back(k);
+    for (int k : ks) {
+      std::vector<zi_system*> set;
+      double rest = 0.0;
+      for (int r = 0; r < nb; ++r) {
+        if (r < k) set.push_back(sys[order[r]]);
+        else rest += c[order[r]];
+      }
+      double t = 0.0;
+      rs = o->precision == ZI_MIXED ? time_persistent<float>(set, o, st, &t) : time_persistent<double>(set, o, st, &t);
+      if (rs != ZI_OK) break;
+      if (k == nb) t_all = t;
+      if (t + rest < best) {
+        best = t + rest;
+        best_k = k;
+      }
+    }
+    cudaStreamDestroy(st);
+    ZI_CHECK(rs);
+    for (int r = 0; r < best_k; ++r) e.persistent[order[r]] = 1;
+    e.est_plan = best;
+    e.est_per_head = all_alone;
+    e.est_persistent = t_all;
+  }
+  std::copy(e.persistent.begin(), e.persistent.end(), persistent);
+  if (info) {
+    info->source = ZI_BATCH_TUNED;
+    info->est_window_ms = e.est_plan;
+    info->est_window_ms_per_head = e.est_per_head;
+    info->est_window_ms_persistent = e.est_persistent;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = e;
+  return ZI_OK;
+}
+
+int check_batch(zi_system* const* sys, int nb, const zi_solver_opts* o) {
+  if (!sys || nb < 1) return set_error(ZI_ERR_ARG, "need at least one system");
+  ZI_CHECK(check_opts(o));
+  for (int b = 0; b < nb; ++b) {
+    if (!sys[b]) return set_error(ZI_ERR_ARG, "null system %d", b);
+    for (int c = 0; c < b; ++c)
+      if (sys[c] == sys[b]) return set_error(ZI_ERR_ARG, "system %d appears twice", b);
+  }
+  return ZI_OK;
+}
+
+// The heads marked persistent in one persistent launch, then the others one
+// after another on the per-head path.
+int run_schedule(zi_system* const* sys, int nb, const zi_solver_opts* o, double* const* T, int32_t* const* iters,
+                 const int32_t* persistent, int chunk, cudaStream_t s) {
+  std::vector<zi_system*> ps;
+  std::vector<double*> pt;
+  std::vector<int32_t*> pi;
+  for (int b = 0; b < nb; ++b)
+    if (persistent[b]) {
+      ps.push_back(sys[b]);
+      pt.push_back(T ? T[b] : nullptr);
+      pi.push_back(iters ? iters[b] : nullptr);
+    }
+  int status = ZI_OK;
+  if (!ps.empty()) {
+    const int st = transfer_batched_impl(ps.data(), (int)ps.size(), o, pt.data(), pi.data(), s, chunk);
+    if (st != ZI_OK && st != ZI_ERR_NOT_CONVERGED) return st;
+    if (st != ZI_OK) status = st;
+  }
+  for (int b = 0; b < nb; ++b) {
+    if (persistent[b]) continue;
+    const int st = transfer_impl(sys[b], o, T ? T[b] : nullptr, iters ? iters[b] : nullptr, nullptr, s);
+    if (st != ZI_OK && st != ZI_ERR_NOT_CONVERGED) return st;
+    if (st != ZI_OK) status = st;
+  }
+  if (status != ZI_OK) return set_error(status, "a head missed tol=%g in the batched solve", o->tol);
+  return ZI_OK;
+}
+
+}  // namespace
+
+extern "C" int zi_batch_tune(zi_system* const* sys, int nb, const zi_solver_opts* o, int32_t* persistent,
+                             zi_batch_schedule* info, cudaStream_t s) {
+  ZI_CHECK(check_batch(sys, nb, o));
+  if (!persistent) return set_error(ZI_ERR_ARG, "null schedule output");
+  return batch_tune(sys, nb, o, persistent, info, s);
+}
+
+extern "C" int zi_transfer_batched_schedule(zi_system* const* sys, int nb, const zi_solver_opts* o, double* const* T,
+                                            int32_t* const* iters, const int32_t* persistent, int chunk,
+                                            cudaStream_t s) {
+  ZI_CHECK(check_batch(sys, nb, o));
+  if (!persistent) return set_error(ZI_ERR_ARG, "null schedule");
+  if (chunk < 0) return set_error(ZI_ERR_ARG, "negative chunk");
+  return run_schedule(sys, nb, o, T, iters, persistent, chunk, s);
+}
+
 extern "C" int zi_transfer(zi_system* S, const zi_solver_opts* o, double* T, int32_t* iters, double* relres,
                            cudaStream_t s) {
   if (!S) return set_error(ZI_ERR_ARG, "null system");
@@ -2603,14 +3020,10 @@ extern "C" int zi_transfer(zi_system* S, const zi_solver_opts* o, double* T, int
 
 extern "C" int zi_transfer_batched(zi_system* const* sys, int nb, const zi_solver_opts* o, double* const* T,
                                    int32_t* const* iters, cudaStream_t s) {
-  if (!sys || nb < 1) return set_error(ZI_ERR_ARG, "need at least one system");
-  ZI_CHECK(check_opts(o));
-  for (int b = 0; b < nb; ++b) {
-    if (!sys[b]) return set_error(ZI_ERR_ARG, "null system %d", b);
-    for (int c = 0; c < b; ++c)
-      if (sys[c] == sys[b]) return set_error(ZI_ERR_ARG, "system %d appears twice", b);
-  }
-  return transfer_batched_impl(sys, nb, o, T, iters, s);
+  ZI_CHECK(check_batch(sys, nb, o));
+  std::vector<int32_t> persistent(nb, 0);
+  ZI_CHECK(batch_tune(sys, nb, o, persistent.data(), nullptr, s));
+  return run_schedule(sys, nb, o, T, iters, persistent.data(), PERSISTENT_CHUNK, s);
 }
 
 namespace zi {
@@ -2619,18 +3032,35 @@ __global__ void k_flush(int64_t n, float* __restrict__ buf, float v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     buf[i] = v;
 }
-}  // namespace
-}  // namespace zi
 
-extern "C" int zi_time_spmm(zi_system* S, int precision, int reps, double* ms_per_launch, double* bytes_per_launch,
-                            cudaStream_t user) {
-  if (!S || !ms_per_launch || reps < 1) return set_error(ZI_ERR_ARG, "bad arguments");
+// X (n x ncol, FP64) into the solver's padded layout (n x ld, type T), zero
+// beyond column ncol; and back.
+template <typename T>
+__global__ void k_pad_in(int64_t n, int ncol, int ld, const double* __restrict__ X, T* __restrict__ P) {
+  const int64_t tot = n * (int64_t)ld;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ld;
+    const int c = (int)(e - i * ld);
+    P[e] = c < ncol ? (T)X[i * ncol + c] : T(0);
+  }
+}
+template <typename T>
+__global__ void k_pad_out(int64_t n, int ncol, int ld, const T* __restrict__ Q, double* __restrict__ Y) {
+  const int64_t tot = n * (int64_t)ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ncol;
+    const int c = (int)(e - i * ncol);
+    Y[e] = (double)Q[i * ld + c];
+  }
+}
+}  // namespace
+
+// The CG plan of a system whose solver matrices are prepared: FP64 (CSR on
+// the compacted pattern) or FP32 (the ELL copy in difference form).
+CgPlan solver_plan(zi_system* S, bool f32) {
   SolverScratch* w = S->solver;
-  if (!w || !w->values_ready || (precision == ZI_MIXED && !w->x32))
-    return set_error(ZI_ERR_ARG, "run zi_transfer with this precision first");
   int ld_, c64, c32;
   choose_layout(S->n_rhs, &ld_, &c64, &c32);
-  const bool f32 = precision == ZI_MIXED;
   CgPlan p = make_plan(S, w, f32 ? c32 : c64, f32 ? 4 : 2);
   if (f32) {
     p.rowptr = w->rowptr32;
@@ -2646,12 +3076,91 @@ extern "C" int zi_time_spmm(zi_system* S, int precision, int reps, double* ms_pe
   } else {
     size_grids<double>(p);
   }
+  return p;
+}
+}  // namespace zi
+
+extern "C" int zi_apply_operator(zi_system* S, const zi_solver_opts* o, const double* X, double* Y, double* dots,
+                                 cudaStream_t user) {
+  if (!S || !o || (S->n > 0 && (!X || !Y))) return set_error(ZI_ERR_ARG, "null argument");
+  ZI_CHECK(check_opts(o));
+  ZI_CHECK(ensure_scratch(S, o, user));
+  SolverScratch* w = S->solver;
+  const cudaStream_t st = w->stream;
+  EventSet evs;
+  ZI_CUDA(evs.create(1, cudaEventDisableTiming));
+  ZI_CUDA(cudaEventRecord(evs[0], user));
+  ZI_CUDA(cudaStreamWaitEvent(st, evs[0], 0));
+  ZI_CHECK(prepare_matrices(S, o, st));
+  const bool f32 = o->precision == ZI_MIXED;
+  const CgPlan p = solver_plan(S, f32);
+  const int64_t n = S->n;
+  const int ld = w->ld, ncol = S->n_rhs;
+  ZI_CUDA(cudaMemsetAsync(w->cnt + 4, 0, sizeof(int), st));
+  if (f32) {
+    k_pad_in<float><<<grid_for(n * ld, 256), 256, 0, st>>>(n, ncol, ld, X, w->p32);
+    ZI_LAUNCH_CHECK();
+    ZI_CHECK(plan_spmm<float>(p, w->v32, w->p32, w->q32, w->part0, st));
+    k_pad_out<float><<<grid_for(n * ncol, 256), 256, 0, st>>>(n, ncol, ld, w->q32, Y);
+    ZI_LAUNCH_CHECK();
+  } else {
+    k_pad_in<double><<<grid_for(n * ld, 256), 256, 0, st>>>(n, ncol, ld, X, w->P);
+    ZI_LAUNCH_CHECK();
+    ZI_CHECK(plan_spmm<double>(p, w->v64, w->P, w->Q, w->part0, st));
+    k_pad_out<double><<<grid_for(n * ncol, 256), 256, 0, st>>>(n, ncol, ld, w->Q, Y);
+    ZI_LAUNCH_CHECK();
+  }
+  if (dots) {
+    k_sum_partials<<<1, FIN_THREADS, 0, st>>>(p.g_spmm / CLUSTER, ld, w->part0, w->vec);
+    ZI_LAUNCH_CHECK();
+    ZI_CUDA(cudaMemcpyAsync(dots, w->vec, sizeof(double) * ncol, cudaMemcpyDeviceToDevice, st));
+  }
+  int herr = 0;
+  ZI_CUDA(cudaMemcpyAsync(&herr, w->cnt + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ZI_CUDA(cudaEventRecord(evs[0], st));
+  ZI_CUDA(cudaStreamWaitEvent(user, evs[0], 0));
+  ZI_CUDA(cudaStreamSynchronize(st));
+  if (herr) ZI_CUDA(cudaMemsetAsync(w->cnt + 4, 0, sizeof(int), st));
+  return device_error_to_status(herr);
+}
+
+extern "C" int zi_solver_get_info(const zi_system* S, zi_solver_info* info) {
+  if (!S || !info) return set_error(ZI_ERR_ARG, "null argument");
+  memset(info, 0, sizeof(*info));
+  int ld, c64, c32;
+  choose_layout(S->n_rhs, &ld, &c64, &c32);
+  info->ld = ld;
+  info->threads_per_row64 = (ld / 2) / c64;
+  info->vectors_per_thread64 = c64;
+  info->threads_per_row32 = (ld / 4) / c32;
+  info->vectors_per_thread32 = c32;
+  const SolverScratch* w = S->solver;
+  if (!w) return ZI_OK;
+  if (w->values_ready) info->nnz64 = w->nnzc;
+  if (w->v32_ready) {
+    info->nnz32 = w->nnz32;
+    info->tail_rows = w->tail_rows;
+    info->tail_entries = w->ntail;
+    info->spmm32 = w->ovf_ci ? ZI_SPMM32_ELL_OVERFLOW : ZI_SPMM32_ELL;
+    info->ell_tiled = w->ell_tiled ? 1 : 0;
+  }
+  return ZI_OK;
+}
+
+extern "C" int zi_time_spmm(zi_system* S, int precision, int reps, double* ms_per_launch, double* bytes_per_launch,
+                            cudaStream_t user) {
+  if (!S || !ms_per_launch || reps < 1) return set_error(ZI_ERR_ARG, "bad arguments");
+  SolverScratch* w = S->solver;
+  if (!w || !w->values_ready || (precision == ZI_MIXED && !w->x32))
+    return set_error(ZI_ERR_ARG, "run zi_transfer with this precision first");
+  const bool f32 = precision == ZI_MIXED;
+  CgPlan p = solver_plan(S, f32);
   cudaStream_t st = w->stream;
   const int64_t nflush = 64ll << 20;  // 64 Mi floats = 256 MB
   DevTmp<float> flush;
   ZI_CHECK(flush.alloc(nflush, st));
-  std::vector<cudaEvent_t> ev(2 * reps);
-  for (auto& e : ev) ZI_CUDA(cudaEventCreate(&e));
+  EventSet ev;
+  ZI_CUDA(ev.create(2 * (size_t)reps));
   for (int r = 0; r < reps; ++r) {
     k_flush<<<sm_count() * 8, 256, 0, st>>>(nflush, flush.p, (float)r);
     ZI_LAUNCH_CHECK();
@@ -2669,7 +3178,6 @@ extern "C" int zi_time_spmm(zi_system* S, int precision, int reps, double* ms_pe
     ZI_CUDA(cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]));
     tot += ms;
   }
-  for (auto& e : ev) cudaEventDestroy(e);
   *ms_per_launch = tot / reps;
   if (bytes_per_launch) {
     const double w_ = f32 ? 4.0 : 8.0;

@@ -28,11 +28,15 @@ STENCIL_WIDTH = 8
 
 # Every symbol include/zi.h declares.
 EXPORTS = ("zi_version", "zi_last_error", "zi_status_string", "zi_mesh_from_grid", "zi_locate_dipoles_grid",
-           "zi_mesh_from_surfaces", "zi_nearest_source", "zi_assemble", "zi_system_set_conductivity",
+           "zi_mesh_from_surfaces", "zi_nearest_source", "zi_locate_points", "zi_leadfield_at", "zi_assemble", "zi_system_set_conductivity",
            "zi_system_get_info", "zi_system_get_matrix", "zi_system_destroy", "zi_solver_opts_default",
            "zi_transfer", "zi_transfer_batched", "zi_leadfield", "zi_source_stencil", "zi_leadfield_sparse",
            "zi_source_pi", "zi_meg_rhs", "zi_meg_transfer", "zi_meg_leadfield", "zi_eit_jacobian",
-           "zi_leadfield_noalloc", "zi_ias_map", "zi_time_spmm", "zi_time_source_apply", "zi_kernel_launches")
+           "zi_leadfield_noalloc", "zi_ias_map", "zi_time_spmm", "zi_time_source_apply", "zi_apply_operator",
+           "zi_solver_get_info", "zi_batch_tune", "zi_transfer_batched_schedule", "zi_memory_stats",
+           "zi_kernel_launches")
+
+SPMM32_NONE, SPMM32_ELL, SPMM32_ELL_OVERFLOW = 0, 1, 2
 
 
 class ZiError(RuntimeError):
@@ -55,6 +59,23 @@ class _Info(ctypes.Structure):
                 ("n_el", ctypes.c_int32), ("n_rhs", ctypes.c_int32), ("n_rows_L", ctypes.c_int32),
                 ("model", ctypes.c_int32), ("ground", ctypes.c_int64), ("n_patch_faces", ctypes.c_int64),
                 ("has_T", ctypes.c_int32)]
+
+
+class _SolverInfo(ctypes.Structure):
+    _fields_ = [("ld", ctypes.c_int32), ("threads_per_row64", ctypes.c_int32),
+                ("vectors_per_thread64", ctypes.c_int32), ("threads_per_row32", ctypes.c_int32),
+                ("vectors_per_thread32", ctypes.c_int32), ("spmm32", ctypes.c_int32),
+                ("nnz64", ctypes.c_int64), ("nnz32", ctypes.c_int64), ("tail_rows", ctypes.c_int64),
+                ("tail_entries", ctypes.c_int64), ("ell_tiled", ctypes.c_int32)]
+
+
+class _BatchSchedule(ctypes.Structure):
+    _fields_ = [("source", ctypes.c_int32), ("est_window_ms", ctypes.c_double),
+                ("est_window_ms_per_head", ctypes.c_double),
+                ("est_window_ms_persistent", ctypes.c_double)]
+
+
+BATCH_TUNED, BATCH_CACHED = 1, 2
 
 
 class _Opts(ctypes.Structure):
@@ -83,6 +104,8 @@ def load_library(path: str = LIB_PATH):
         "zi_mesh_from_grid": ([D, ctypes.c_int, P, P, P, P, P, P, P, P, P], ctypes.c_int),
         "zi_locate_dipoles_grid": ([D, ctypes.c_int, P, P, I64, P, P], ctypes.c_int),
         "zi_nearest_source": ([P, I64, P, I64, P, P], ctypes.c_int),
+        "zi_locate_points": ([P, I64, P, I64, P, I64, P, P], ctypes.c_int),
+        "zi_leadfield_at": ([P, P, I64, ctypes.POINTER(_Opts), P, P], ctypes.c_int),
         "zi_mesh_from_surfaces": ([D, ctypes.c_int, P, P, P, I64, P, P, P, P, P, P, P, P, P], ctypes.c_int),
         "zi_assemble": ([P, I64, P, I64, P, P, I64, ctypes.POINTER(_Electrodes), P, P], ctypes.c_int),
         "zi_system_set_conductivity": ([P, P, P], ctypes.c_int),
@@ -105,6 +128,13 @@ def load_library(path: str = LIB_PATH):
         "zi_time_spmm": ([P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(D), ctypes.POINTER(D), P], ctypes.c_int),
         "zi_time_source_apply": ([P, P, P, I64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(D),
                                   ctypes.POINTER(D), P], ctypes.c_int),
+        "zi_apply_operator": ([P, ctypes.POINTER(_Opts), P, P, P, P], ctypes.c_int),
+        "zi_solver_get_info": ([P, ctypes.POINTER(_SolverInfo)], ctypes.c_int),
+        "zi_batch_tune": ([P, ctypes.c_int, ctypes.POINTER(_Opts), P, ctypes.POINTER(_BatchSchedule), P],
+                          ctypes.c_int),
+        "zi_transfer_batched_schedule": ([P, ctypes.c_int, ctypes.POINTER(_Opts), P, P, P, ctypes.c_int, P],
+                                         ctypes.c_int),
+        "zi_memory_stats": ([P, P, ctypes.c_int], ctypes.c_int),
         "zi_kernel_launches": ([], ctypes.c_int64),
     }
     for name, (args, res) in sig.items():
@@ -188,6 +218,15 @@ def version() -> int:
     return load_library().zi_version()
 
 
+def memory_stats(reset_high: bool = False):
+    """(bytes in use, high-water mark) of the library's device-memory pool on
+    the current device (zi_memory_stats); reset_high zeroes the mark after
+    reading it."""
+    now, high = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().zi_memory_stats(ctypes.byref(now), ctypes.byref(high), int(bool(reset_high))))
+    return now.value, high.value
+
+
 def kernel_launches() -> int:
     """libzi kernels launched by this process so far (zi_kernel_launches)."""
     return int(load_library().zi_kernel_launches())
@@ -246,6 +285,20 @@ def mesh_from_surfaces(h: float, surfaces, priority, device="cuda"):
     _check(lib.zi_mesh_from_surfaces(*args, ctypes.byref(n), ctypes.byref(m), ctypes.byref(nb),
                                      _ptr(nodes), _ptr(tets), _ptr(labels), _ptr(bfaces), st))
     return dict(nodes=nodes, tets=tets, labels=labels, bfaces=bfaces, h=float(h))
+
+
+def locate_points(nodes, tets, pos, device="cuda"):
+    """Element of the mesh (nodes, tets) holding each position
+    (zi_locate_points), as an int32 CUDA tensor."""
+    torch = _torch()
+    lib = load_library()
+    V = _dev(nodes, torch.float64, device).reshape(-1, 3).contiguous()
+    T = _dev(tets, torch.int32, device).reshape(-1, 4).contiguous()
+    X = _dev(pos, torch.float64, device).reshape(-1, 3).contiguous()
+    out = torch.empty(X.shape[0], dtype=torch.int32, device=device)
+    _check(lib.zi_locate_points(_ptr(V), V.shape[0], _ptr(T), T.shape[0], _ptr(X), X.shape[0], _ptr(out),
+                                _stream()))
+    return out
 
 
 def nearest_source(points, sources, device="cuda"):
@@ -354,6 +407,20 @@ class System:
                                                     device=self.nodes.device)
         o = opts.c()
         _check(self._lib.zi_leadfield(self._h, _ptr(dt), P, ctypes.byref(o), _ptr(L), _stream()))
+        return L
+
+    def leadfield_at(self, pos, opts: SolverOpts | None = None, out=None):
+        """L (zi_leadfield_at) for dipoles at positions pos (P x 3, metres),
+        located on the system's own mesh; columns 3p + d."""
+        torch = _torch()
+        opts = opts or SolverOpts()
+        ps = _dev(pos, torch.float64, self.nodes.device).reshape(-1, 3).contiguous()
+        inf = self.info()
+        P = ps.shape[0]
+        L = out if out is not None else torch.empty((inf["n_rows_L"], 3 * P), dtype=torch.float64,
+                                                    device=self.nodes.device)
+        o = opts.c()
+        _check(self._lib.zi_leadfield_at(self._h, _ptr(ps), P, ctypes.byref(o), _ptr(L), _stream()))
         return L
 
     def source_stencil(self, pos, dip_tet, model=SOURCE_PBO10, lam: float = 0.0):
@@ -496,6 +563,25 @@ class System:
         _check(self._lib.zi_time_spmm(self._h, precision, reps, ctypes.byref(ms), ctypes.byref(by), _stream()))
         return ms.value, by.value
 
+    def apply_operator(self, X, opts: "SolverOpts", want_dots=True):
+        """(Y, dots): the solver's own operator applied to X (n x n_rhs) with its
+        fused column dots (zi_apply_operator): S A S X for FP64, the FP32
+        difference-form A X for MIXED."""
+        torch = _torch()
+        X = _dev(X, torch.float64, self.nodes.device)
+        inf = self.info()
+        Y = torch.empty((inf["n"], inf["n_rhs"]), dtype=torch.float64, device=X.device)
+        dots = torch.empty(inf["n_rhs"], dtype=torch.float64, device=X.device) if want_dots else None
+        o = opts.c()
+        _check(self._lib.zi_apply_operator(self._h, ctypes.byref(o), _ptr(X), _ptr(Y), _ptr(dots), _stream()))
+        return Y, dots
+
+    def solver_info(self) -> dict:
+        """The solver's layout and matrix-copy sizes (zi_solver_get_info)."""
+        inf = _SolverInfo()
+        _check(self._lib.zi_solver_get_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in _SolverInfo._fields_}
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.zi_system_destroy(self._h)
@@ -508,9 +594,28 @@ class System:
             pass
 
 
-def transfer_batched(systems, opts: SolverOpts | None = None, want_T: bool = False):
+def batch_tune(systems, opts: SolverOpts | None = None):
+    """The autotuner's schedule for this batch (zi_batch_tune): (list of 0/1,
+    1 = head in the persistent launch; dict with the source and the
+    estimated ms per iteration of the schedule, of every head alone, and of
+    every head in the persistent launch)."""
+    lib = load_library()
+    opts = opts or SolverOpts()
+    nb = len(systems)
+    hs = (ctypes.c_void_p * nb)(*[s.handle.value for s in systems])
+    mask = (ctypes.c_int32 * nb)()
+    info = _BatchSchedule()
+    o = opts.c()
+    _check(lib.zi_batch_tune(hs, nb, ctypes.byref(o), mask, ctypes.byref(info), _stream()))
+    return list(mask), {k: getattr(info, k) for k, _ in _BatchSchedule._fields_}
+
+
+def transfer_batched(systems, opts: SolverOpts | None = None, want_T: bool = False, persistent=None,
+                     chunk: int = 0):
     """Transfer matrices of several systems in one batched solve
-    (zi_transfer_batched); returns (list of T or None, list of iters)."""
+    (zi_transfer_batched, the tuned schedule; or zi_transfer_batched_schedule
+    when `persistent` gives the schedule: one 0/1 per system); returns (list
+    of T or None, list of iters)."""
     torch = _torch()
     lib = load_library()
     opts = opts or SolverOpts()
@@ -526,7 +631,13 @@ def transfer_batched(systems, opts: SolverOpts | None = None, want_T: bool = Fal
         its.append(it)
         itp[b] = ctypes.cast(it, ctypes.c_void_p).value
     o = opts.c()
-    _check(lib.zi_transfer_batched(hs, nb, ctypes.byref(o), Tp, itp, _stream()))
+    if persistent is None:
+        _check(lib.zi_transfer_batched(hs, nb, ctypes.byref(o), Tp, itp, _stream()))
+    else:
+        if len(persistent) != nb:
+            raise ValueError("one schedule flag per system")
+        mask = (ctypes.c_int32 * nb)(*[1 if p else 0 for p in persistent])
+        _check(lib.zi_transfer_batched_schedule(hs, nb, ctypes.byref(o), Tp, itp, mask, int(chunk), _stream()))
     return Ts, [np.array(it[:], dtype=np.int32) for it in its]
 
 

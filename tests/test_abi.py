@@ -75,6 +75,14 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.zi_meg_rhs(None, None, None, None, 4, None, None) == zi.ZI_ERR_ARG
     assert lib.zi_meg_transfer(None, None, None, None, 4, None, None, None, None, None) == zi.ZI_ERR_ARG
     assert lib.zi_meg_leadfield(None, None, None, None, 4, None, 1, None, None, 4, None, None) == zi.ZI_ERR_ARG
+    o = zi._Opts()
+    lib.zi_solver_opts_default(ctypes.byref(o))
+    assert lib.zi_apply_operator(None, ctypes.byref(o), None, None, None, None) == zi.ZI_ERR_ARG
+    assert lib.zi_solver_get_info(None, None) == zi.ZI_ERR_ARG
+    assert lib.zi_locate_points(None, 0, None, 0, None, 1, None, None) == zi.ZI_ERR_ARG
+    assert lib.zi_leadfield_at(None, None, 1, ctypes.byref(o), None, None) == zi.ZI_ERR_ARG
+    assert lib.zi_batch_tune(None, 0, ctypes.byref(o), None, None, None) == zi.ZI_ERR_ARG
+    assert lib.zi_transfer_batched_schedule(None, 0, ctypes.byref(o), None, None, None, 0, None) == zi.ZI_ERR_ARG
 
 
 def test_default_solver_options(lib):

@@ -1,5 +1,6 @@
-"""Batched transfer solve: many heads of different sizes and electrode counts
-in one persistent launch, against per-head solves and the oracle."""
+"""Batched transfer solve: many heads of different sizes and electrode counts,
+in the autotuned schedule and with every head in the persistent launch,
+against per-head solves and the oracle; the autotuner's choice and cache."""
 import numpy as np
 import pytest
 
@@ -39,12 +40,14 @@ def _build(spec):
     return system, dip
 
 
+@pytest.mark.parametrize("schedule", ["tuned", "persistent"])
 @pytest.mark.parametrize("precision", [zi.FP64, zi.MIXED], ids=["fp64", "mixed"])
-def test_batched_matches_per_head_solves(precision):
+def test_batched_matches_per_head_solves(precision, schedule):
     opts = zi.SolverOpts(tol=1e-10, precision=precision)
     built = [_build(sp) for sp in SPECS]
     systems = [b[0] for b in built]
-    Tb, itb = zi.transfer_batched(systems, opts, want_T=True)
+    Tb, itb = zi.transfer_batched(systems, opts, want_T=True,
+                                  persistent=None if schedule == "tuned" else [1] * len(systems))
     for (system, dip), spec, T, it in zip(built, SPECS, Tb, itb):
         assert np.all(it > 0)
         single = _build(spec)[0]
@@ -88,12 +91,33 @@ def test_barrier_timeout_is_reported_and_context_survives(monkeypatch):
     opts = zi.SolverOpts(tol=1e-10, precision=zi.FP64)
     monkeypatch.setenv("ZI_TEST_BARRIER_SKIP", "1")
     with pytest.raises(zi.ZiError) as e:
-        zi.transfer_batched(systems, opts)
+        zi.transfer_batched(systems, opts, persistent=[1, 1])
     assert e.value.status == zi.ZI_ERR_TIMEOUT
     monkeypatch.delenv("ZI_TEST_BARRIER_SKIP")
-    Tb, itb = zi.transfer_batched(systems, opts, want_T=True)
+    Tb, itb = zi.transfer_batched(systems, opts, want_T=True, persistent=[1, 1])
     single = _build(SPECS[0])[0]
     Ts, _, _ = single.transfer(opts)
     assert rel(Tb[0].cpu().numpy(), Ts.cpu().numpy()) < 1e-8
     for s in systems + [single]:
+        s.close()
+
+
+def test_autotuner_picks_the_fastest_estimate_and_caches_it():
+    """The tuned schedule's estimated time per iteration is no worse than
+    every head alone or every head in the persistent launch (both are
+    candidates); a second call of the same signature comes from the cache."""
+    opts = zi.SolverOpts(tol=1e-10, precision=zi.MIXED)
+    systems = [_build(sp)[0] for sp in SPECS[::-1]]
+    mask, info = zi.batch_tune(systems, opts)
+    assert info["source"] == zi.BATCH_TUNED and len(mask) == len(systems)
+    assert info["est_window_ms"] <= info["est_window_ms_per_head"]
+    assert info["est_window_ms"] <= info["est_window_ms_persistent"]
+    assert sum(mask) != 1                       # a persistent set of one head is never chosen
+    mask2, info2 = zi.batch_tune(systems, opts)
+    assert info2["source"] == zi.BATCH_CACHED and mask2 == mask
+    Tb, _ = zi.transfer_batched(systems, opts, want_T=True)
+    Tp, _ = zi.transfer_batched(systems, opts, want_T=True, persistent=mask, chunk=16)
+    for a, b in zip(Tb, Tp):
+        assert torch.equal(a, b)               # zi_transfer_batched runs the cached schedule
+    for s in systems:
         s.close()

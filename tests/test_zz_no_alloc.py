@@ -53,10 +53,16 @@ def test_noalloc_lead_field_matches_zi_leadfield_twice(spec):
     system.transfer(zi.SolverOpts(tol=1e-10))
     L_ref = system.leadfield(dip).cpu().numpy()
     rows = system.info()["n_rows_L"]
+    torch.cuda.synchronize()
+    used0, _ = zi.memory_stats(reset_high=True)
     for _ in range(2):  # the scratch keeps the previous call's contents
         L = _noalloc(system, dip, rows)
         assert np.all(np.isfinite(L))
         assert np.linalg.norm(L - L_ref) <= TOL * np.linalg.norm(L_ref)
+    # nothing was drawn from the library's pool: its high-water mark, zeroed
+    # before the calls, stays at or below what was in use before them
+    _, high = zi.memory_stats()
+    assert high <= used0
     system.close()
 
 
