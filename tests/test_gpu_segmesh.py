@@ -2,9 +2,9 @@
 interpolation through the C ABI: nodes, tets, labels and boundary faces
 bit-exact against the oracle on surfaces kept off the grid nodes (so every
 label is decided far from the winding number's threshold), the lead field of
-the GPU mesh against the oracle's, nearest-DOF indices bit-exact, empty inputs
-of the source and sensor calls, and the error paths the kernels check.  (The
-file sorts last: its kernels' first GPU run cannot hide another test.)"""
+the GPU mesh (from dipole positions) against the oracle's, nearest-DOF indices
+bit-exact, empty inputs of the source and sensor calls, and the error paths the
+kernels check."""
 import numpy as np
 import pytest
 
