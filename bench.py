@@ -50,8 +50,11 @@ DEFAULT_WORKLOAD = "aniso1mm"
 # ncu DRAM traffic per launch of the FP32 SpMM on this workload, from the capture
 # summarised in profiles/ (None until taken, or once the kernel source changed).
 SPMM_TRAFFIC = {
-    "shell2mm": {"source_sha": "8e30f73bd16fd9df", "bytes": 246.94656e6 + 184.47488e6,
-                 "note": "one ncu capture of the standalone launch on this workload"},
+    "shell2mm": {"source_sha": "d5822d00ddfba050", "bytes": 246.967552e6 + 184.626944e6,
+                 "note": "one ncu capture (--set full) of the standalone launch on this workload"},
+    "aniso1mm": {"source_sha": "d5822d00ddfba050", "bytes": 5.33e9 + 3.39e9,
+                 "note": "one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the "
+                         "standalone launch on this workload at full size"},
 }
 
 
