@@ -50,9 +50,9 @@ DEFAULT_WORKLOAD = "aniso1mm"
 # ncu DRAM traffic per launch of the FP32 SpMM on this workload, from the capture
 # summarised in profiles/ (None until taken, or once the kernel source changed).
 SPMM_TRAFFIC = {
-    "shell2mm": {"source_sha": "d5822d00ddfba050", "bytes": 246.967552e6 + 184.626944e6,
+    "shell2mm": {"source_sha": "773b0a3cd13d3b2b", "bytes": 246.967552e6 + 184.626944e6,
                  "note": "one ncu capture (--set full) of the standalone launch on this workload"},
-    "aniso1mm": {"source_sha": "d5822d00ddfba050", "bytes": 5.33e9 + 3.39e9,
+    "aniso1mm": {"source_sha": "773b0a3cd13d3b2b", "bytes": 5.33e9 + 3.39e9,
                  "note": "one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the "
                          "standalone launch on this workload at full size"},
 }
@@ -310,17 +310,19 @@ def measured_peak_gbs():
 
 def spmm_source_sha():
     """Hash of the source the FP32 ELL SpMM is compiled from: the shared
-    header and zi_pcg.cu up to the end of k_spmm_ell (everything after it --
-    the vector kernels, the batched kernel, the host code -- cannot change
-    the SpMM's code)."""
+    header and zi_pcg.cu from its first include to the end of k_spmm_ell
+    (the file's leading comment and everything after the kernel -- the vector
+    kernels, the batched kernel, the host code -- cannot change the SpMM's
+    code)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1811_07717_gb300", "csrc")
     with open(os.path.join(csrc, "zi_internal.cuh"), "rb") as f:
         head = f.read()
     with open(os.path.join(csrc, "zi_pcg.cu"), "rb") as f:
         body = f.read()
+    start = max(body.find(b"#include"), 0)
     end = body.find(b"// r -= alpha q, with the column partials")
-    return hashlib.sha256(head + (body[:end] if end > 0 else body)).hexdigest()[:16]
+    return hashlib.sha256(head + (body[start:end] if end > 0 else body[start:])).hexdigest()[:16]
 
 
 # ---------------------------------------------------------------------------

@@ -216,6 +216,12 @@ int zi_assemble(const double* nodes, int64_t n, const int32_t* tets, int64_t m,
  * electrodes and pattern); invalidates a previously computed T. */
 int zi_system_set_conductivity(zi_system* sys, const double* sigma6, cudaStream_t stream);
 
+/* The same for the log-conductivity parametrisation of the linearised EIT
+ * (App. A.3): element e's tensor is exp(log_s[e]) times its base tensor,
+ * formed on the device (sigma_base6: device m x 6 f64; log_s: device m f64). */
+int zi_system_set_log_conductivity(zi_system* sys, const double* sigma_base6, const double* log_s,
+                                   cudaStream_t stream);
+
 typedef struct zi_system_info {
   int64_t n;          /* nodes */
   int64_t m;          /* tets */

@@ -712,6 +712,30 @@ extern "C" int zi_system_set_conductivity(zi_system* S, const double* sigma6, cu
   return ZI_OK;
 }
 
+namespace zi {
+namespace {
+// sigma_e = exp(log_s_e) * base_e, all six tensor entries of element e.
+__global__ void k_scale_sigma(int64_t m, const double* __restrict__ base6, const double* __restrict__ log_s,
+                              double* __restrict__ out6) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const double f = exp(log_s[e]);
+    for (int k = 0; k < 6; ++k) out6[6 * e + k] = f * base6[6 * e + k];
+  }
+}
+}  // namespace
+}  // namespace zi
+
+extern "C" int zi_system_set_log_conductivity(zi_system* S, const double* sigma_base6, const double* log_s,
+                                              cudaStream_t s) {
+  if (!S || !sigma_base6 || !log_s) return set_error(ZI_ERR_ARG, "null argument");
+  DevTmp<double> s6;
+  ZI_CHECK(s6.alloc(6 * (size_t)S->m, s));
+  k_scale_sigma<<<grid_for(S->m, 256), 256, 0, s>>>(S->m, sigma_base6, log_s, s6.p);
+  ZI_LAUNCH_CHECK();
+  ZI_CHECK(assemble_values(S, s6.p, s));
+  return ZI_OK;
+}
+
 extern "C" int zi_system_get_info(const zi_system* S, zi_system_info* info) {
   if (!S || !info) return set_error(ZI_ERR_ARG, "null argument");
   info->n = S->n;

@@ -44,9 +44,13 @@ inline double dkey_inv(unsigned long long k) {
   return v;
 }
 
-// bounds[0..2] = min keys, bounds[3..5] = max keys
-__global__ void k_node_bounds(int64_t n, const double* __restrict__ nodes, unsigned long long* __restrict__ bounds,
-                              int* __restrict__ err) {
+// bounds[0..2] = min keys, bounds[3..5] = max keys: per-thread extremes,
+// combined in shared memory, one update per block.
+__global__ void __launch_bounds__(256) k_node_bounds(int64_t n, const double* __restrict__ nodes,
+                                                     unsigned long long* __restrict__ bounds,
+                                                     int* __restrict__ err) {
+  __shared__ unsigned long long sk[6][256];
+  unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     for (int d = 0; d < 3; ++d) {
       const double x = nodes[3 * i + d];
@@ -54,10 +58,28 @@ __global__ void k_node_bounds(int64_t n, const double* __restrict__ nodes, unsig
         atomicOr(err, DEV_ERR_NONFINITE);
         continue;
       }
-      atomicMin(bounds + d, dkey(x));
-      atomicMax(bounds + 3 + d, dkey(x));
+      lo[d] = min(lo[d], dkey(x));
+      hi[d] = max(hi[d], dkey(x));
     }
   }
+  for (int d = 0; d < 3; ++d) {
+    sk[d][threadIdx.x] = lo[d];
+    sk[3 + d][threadIdx.x] = hi[d];
+  }
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int d = 0; d < 3; ++d) {
+        sk[d][threadIdx.x] = min(sk[d][threadIdx.x], sk[d][threadIdx.x + w]);
+        sk[3 + d][threadIdx.x] = max(sk[3 + d][threadIdx.x], sk[3 + d][threadIdx.x + w]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int d = 0; d < 3; ++d) {
+      atomicMin(bounds + d, sk[d][0]);
+      atomicMax(bounds + 3 + d, sk[3 + d][0]);
+    }
 }
 
 __device__ __forceinline__ int cell_coord(const CellGrid& g, int d, double x) {

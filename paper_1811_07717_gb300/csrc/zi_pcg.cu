@@ -11,8 +11,10 @@
 //    nonzero.  Each column keeps its own alpha/beta and stops on its own
 //    true residual (columns that converged are frozen with alpha = beta = 0).
 //  * Per iteration: SpMM fused with the p.q column dots; a finalize kernel
-//    (alpha); the x/r update fused with the r.r and D-weighted r.r dots;
-//    a finalize kernel (beta, convergence); the p update.  A chunk of
+//    (alpha); the r update fused with the r.r and D-weighted r.r dots; a
+//    finalize kernel (beta, convergence); the p update, with x += alpha p
+//    (the FP32 inner solve applies x every second iteration, for two
+//    iterations at once, from two direction buffers).  A chunk of
 //    iterations is captured once as a CUDA graph and replayed; the host reads
 //    one counter of active columns per chunk.
 //  * Every reduction has a fixed assignment of rows to threads and a fixed
@@ -615,6 +617,77 @@ __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, int tpr, int ld, cons
   }
 }
 
+// The direction update with x applied every second iteration, so that one
+// pass over x serves two iterations (4.5 vector sweeps per iteration on
+// average instead of 5).  The search direction alternates between two
+// buffers A (even iterations read it) and B (odd iterations read it):
+//   even k: p_{k+1} = z + beta p_k into B; x += alpha_k p_k at once only when
+//           the run stopped after this iteration or `flush` is set (the last
+//           iteration of a run of odd length);
+//   odd k+1: x += alpha_k p_k + alpha_{k+1} p_{k+1}, then p_{k+2} = z +
+//           beta p_{k+1} over p_k in A (each thread reads its p_k before it
+//           writes there).
+// alpha_k of even iterations is kept in a_even, of odd ones in a_odd.
+template <typename T, int CPTV, bool ODD>
+__global__ void __launch_bounds__(256) k_cg_dir2(int64_t n, int tpr, int ld, const double* __restrict__ a_even,
+                                                 const double* __restrict__ a_odd, const double* __restrict__ beta,
+                                                 const T* __restrict__ R, const double* __restrict__ wz,
+                                                 const T* __restrict__ Pcur, T* PA, T* __restrict__ PB,
+                                                 T* __restrict__ X, const int* __restrict__ cnt, int freeze,
+                                                 int flush) {
+  if (cnt && *(volatile const int*)(cnt + 3)) return;
+  const bool upd_x = ODD || flush || run_stopped(cnt, freeze);
+  using V = typename Vec<T>::type;
+  constexpr int W = Vec<T>::W;
+  const int nv = ld / W;
+  const int rpb = blockDim.x / tpr;
+  const int g = threadIdx.x / tpr, c = threadIdx.x % tpr;
+  if (g >= rpb) return;
+  T ae[CPTV][W], ao[CPTV][W], be[CPTV][W];
+#pragma unroll
+  for (int v = 0; v < CPTV; ++v)
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      ae[v][k] = (T)a_even[(c + v * tpr) * W + k];
+      ao[v][k] = ODD ? (T)a_odd[(c + v * tpr) * W + k] : T(0);
+      be[v][k] = (T)beta[(c + v * tpr) * W + k];
+    }
+  const V* Rv = reinterpret_cast<const V*>(R);
+  const V* Pc = reinterpret_cast<const V*>(Pcur);
+  V* Av = reinterpret_cast<V*>(PA);
+  V* Bv = reinterpret_cast<V*>(PB);
+  V* Xv = reinterpret_cast<V*>(X);
+  const RowWalk rw = row_walk(n, rpb, g);
+  int slot = 0;
+  for (int i = rw_first(rw); i >= 0; i = rw_next(rw, i, slot)) {
+    const T wi = wz ? (T)__ldg(wz + i) : T(1);
+#pragma unroll
+    for (int v = 0; v < CPTV; ++v) {
+      const int o = i * nv + c + v * tpr;
+      const V r = ldg_v(Rv + o), pc = Pc[o];
+      V pn;
+#pragma unroll
+      for (int k = 0; k < W; ++k) vset(pn, k, wi * vget(r, k) + be[v][k] * vget(pc, k));
+      if (ODD) {
+        const V pp = Av[o];
+        V x = Xv[o];
+#pragma unroll
+        for (int k = 0; k < W; ++k) vset(x, k, vget(x, k) + ae[v][k] * vget(pp, k) + ao[v][k] * vget(pc, k));
+        Xv[o] = x;
+        Av[o] = pn;
+      } else {
+        Bv[o] = pn;
+        if (upd_x) {
+          V x = Xv[o];
+#pragma unroll
+          for (int k = 0; k < W; ++k) vset(x, k, vget(x, k) + ae[v][k] * vget(pc, k));
+          Xv[o] = x;
+        }
+      }
+    }
+  }
+}
+
 // Column state shared by the finalize kernels.
 struct ColState {
   double* rho;     // r.r (scaled space)
@@ -916,18 +989,32 @@ inline double ord_key_inv(unsigned long long k) {
 }
 
 // keys[0..2]: min coordinate per axis; keys[3]: smallest positive edge extent
-// (the largest |component| of an edge vector: h on a Kuhn grid).
-__global__ void k_ord_extent(int64_t n, const double* __restrict__ nodes, int64_t m, const int32_t* __restrict__ tets,
-                             unsigned long long* __restrict__ keys) {
+// (the largest |component| of an edge vector: h on a Kuhn grid).  Each
+// thread keeps its own minima, the block combines them in shared memory, and
+// one thread per block updates the four keys.
+__global__ void __launch_bounds__(256) k_ord_extent(int64_t n, const double* __restrict__ nodes, int64_t m,
+                                                    const int32_t* __restrict__ tets,
+                                                    unsigned long long* __restrict__ keys) {
+  __shared__ unsigned long long sk[4][256];
+  unsigned long long k[4] = {~0ull, ~0ull, ~0ull, ~0ull};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
-    for (int d = 0; d < 3; ++d) atomicMin(keys + d, ord_key(nodes[3 * i + d]));
+    for (int d = 0; d < 3; ++d) k[d] = min(k[d], ord_key(nodes[3 * i + d]));
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride) {
     const int32_t a = tets[4 * e], b = tets[4 * e + 1];
     double ext = 0.0;
     for (int d = 0; d < 3; ++d) ext = fmax(ext, fabs(nodes[3 * (int64_t)a + d] - nodes[3 * (int64_t)b + d]));
-    if (ext > 0.0) atomicMin(keys + 3, ord_key(ext));
+    if (ext > 0.0) k[3] = min(k[3], ord_key(ext));
   }
+  for (int d = 0; d < 4; ++d) sk[d][threadIdx.x] = k[d];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int d = 0; d < 4; ++d) sk[d][threadIdx.x] = min(sk[d][threadIdx.x], sk[d][threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int d = 0; d < 4; ++d) atomicMin(keys + d, sk[d][0]);
 }
 
 // Grid coordinates of every node; *bad = 1 if a node is off the grid.
@@ -1194,10 +1281,12 @@ struct SolverScratch {
   double *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr;
   // FP32 vectors n x ld
   float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+  float* p32b = nullptr;  // second direction buffer (odd iterations)
   // partials nblk x ld (three)
   double *part0 = nullptr, *part1 = nullptr, *part2 = nullptr;
   // column state (ld each)
   double *rho = nullptr, *alpha = nullptr, *beta = nullptr, *stop2 = nullptr, *bb = nullptr, *vec = nullptr;
+  double* alpha2 = nullptr;  // alpha of odd iterations (x is updated every second iteration)
   int *conv = nullptr, *iters = nullptr, *cnt = nullptr;  // cnt[0] active, cnt[1] iteration, cnt[2] reached
   double *gamma = nullptr, *gamma_prev = nullptr;  // mixed: column scale of the FP32 phase
   int *flag = nullptr, *nact = nullptr;            // mixed: columns within tol / count
@@ -1222,7 +1311,8 @@ void solver_scratch_free(zi_system* S) {
   if (!w) return;
   cudaStream_t s = 0;
   void* ptrs[] = {w->s, w->dtrue, w->w32, w->v64, w->rowptrc, w->colindc, w->valsc, w->v32, w->rowptr32, w->colind32, w->ell_ci, w->ell_va, w->tail_ptr, w->tail_ci, w->tail_va, w->ovf_ci, w->ovf_va, w->X, w->R, w->P, w->Q, w->x32, w->r32, w->p32, w->q32,
-                  w->part0, w->part1, w->part2, w->rho, w->alpha, w->beta, w->stop2, w->bb, w->vec,
+                  w->part0, w->part1, w->part2, w->rho, w->alpha, w->beta, w->stop2, w->bb, w->vec, w->p32b,
+                  w->alpha2,
                   w->conv, w->iters, w->cnt, w->gamma, w->gamma_prev, w->flag, w->nact, w->bar, w->gpart};
   for (void* p : ptrs) dfree(p, s);
   if (w->graph64) cudaGraphExecDestroy(w->graph64);
@@ -1334,6 +1424,31 @@ int launch_dir(int cptv, dim3 grid, int tpr, cudaStream_t st, int64_t n, int ld,
   return ZI_OK;
 }
 
+template <typename T>
+int launch_dir2(bool odd, int cptv, dim3 grid, int tpr, cudaStream_t st, int64_t n, int ld, const double* a_even,
+                const double* a_odd, const double* beta, const T* R, const double* wz, const T* Pcur, T* PA, T* PB,
+                T* X, const int* cnt, int freeze, int flush) {
+#define ZI_DIR2_CASE(CV)                                                                                       \
+  case CV:                                                                                                     \
+    if (odd)                                                                                                   \
+      k_cg_dir2<T, CV, true><<<grid, BLOCK, 0, st>>>(n, tpr, ld, a_even, a_odd, beta, R, wz, Pcur, PA, PB, X, cnt, \
+                                                     freeze, flush);                                           \
+    else                                                                                                       \
+      k_cg_dir2<T, CV, false><<<grid, BLOCK, 0, st>>>(n, tpr, ld, a_even, a_odd, beta, R, wz, Pcur, PA, PB, X,   \
+                                                      cnt, freeze, flush);                                     \
+    break;
+  switch (cptv) {
+    ZI_DIR2_CASE(1)
+    ZI_DIR2_CASE(2)
+    ZI_DIR2_CASE(4)
+    ZI_DIR2_CASE(8)
+    default: return set_error(ZI_ERR_ARG, "unsupported column layout");
+  }
+#undef ZI_DIR2_CASE
+  ZI_LAUNCH_CHECK();
+  return ZI_OK;
+}
+
 int launch_residual(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, int ncol, int ld,
                     const int32_t* rp, const int32_t* ci, const double* v, const double* X, const double* B,
                     double* R, double* part) {
@@ -1430,7 +1545,15 @@ static const void* resid_fn(int cptv) {
   }
 }
 template <typename T>
-static const void* dir_fn(int cptv) {
+static const void* dir_fn(int cptv) {  // FP32: sized by the heavier, odd-iteration variant
+  if constexpr (sizeof(T) == 4) {
+    switch (cptv) {
+      case 1: return (const void*)k_cg_dir2<T, 1, true>;
+      case 2: return (const void*)k_cg_dir2<T, 2, true>;
+      case 4: return (const void*)k_cg_dir2<T, 4, true>;
+      default: return (const void*)k_cg_dir2<T, 8, true>;
+    }
+  }
   switch (cptv) {
     case 1: return (const void*)k_cg_dir<T, 1>;
     case 2: return (const void*)k_cg_dir<T, 2>;
@@ -1483,10 +1606,18 @@ static CgPlan make_plan(zi_system* S, SolverScratch* w, int cptv, int vecw) {
   return p;
 }
 
-// Records `chunk` CG iterations on stream st.
+// The FP32 inner solve applies x every second iteration (k_cg_dir2, two
+// direction buffers); the FP64 path keeps the one-pass update (k_cg_dir): its
+// 4-vector rows made the paired kernel register-bound and 3 % slower.
+template <typename T> constexpr bool paired_dir() { return sizeof(T) == 4; }
+
+// Records `chunk` CG iterations on stream st, starting from an even iteration
+// (direction in P; the FP32 path's other direction buffer is P2, see
+// k_cg_dir2).  flush_last: the run ends after this recording, on an even
+// iteration when chunk is odd, so that iteration applies its own x update.
 template <typename T>
-static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, T* P, T* Q, int chunk,
-                             cudaStream_t st) {
+static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, T* P, T* P2, T* Q,
+                             int chunk, cudaStream_t st, bool flush_last = false) {
   ColState cs{w->rho, w->alpha, w->beta, w->stop2, w->conv, w->iters, w->cnt, w->cnt + 1, w->cnt + 2,
               sizeof(T) == sizeof(double) ? 1 : 0};
   // FP32 inner solve: Jacobi/LDP-preconditioned CG on the unscaled matrix
@@ -1495,20 +1626,28 @@ static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T
   // partials per reduction: one per cluster of each kernel's resident grid
   const int ncl_spmm = p.g_spmm / CLUSTER, ncl_resid = p.g_resid / CLUSTER;
   for (int k = 0; k < chunk; ++k) {
-    ZI_CHECK(plan_spmm<T>(p, vals, P, Q, w->part0, st, w->cnt, cs.freeze));
-    k_fin_alpha<<<1, FIN_THREADS, 0, st>>>(ncl_spmm, p.ld, p.ncol, w->part0, cs);
+    const bool odd = paired_dir<T>() && (k & 1);
+    T* Pc = odd ? P2 : P;
+    ColState ca = cs;
+    ca.alpha = odd ? w->alpha2 : w->alpha;
+    ZI_CHECK(plan_spmm<T>(p, vals, Pc, Q, w->part0, st, w->cnt, cs.freeze));
+    k_fin_alpha<<<1, FIN_THREADS, 0, st>>>(ncl_spmm, p.ld, p.ncol, w->part0, ca);
     ZI_LAUNCH_CHECK();
-    ZI_CHECK(launch_resid<T>(p.cptv, dim3(p.g_resid), p.tpr, p.smem, st, p.n, p.ld, w->alpha, Q, R, w->dtrue,
+    ZI_CHECK(launch_resid<T>(p.cptv, dim3(p.g_resid), p.tpr, p.smem, st, p.n, p.ld, ca.alpha, Q, R, w->dtrue,
                              wpcg, w->part1, w->part2, w->cnt, cs.freeze));
     k_fin_beta<<<1, FIN_THREADS, 0, st>>>(ncl_resid, p.ld, p.ncol, w->part1, w->part2, cs);
     ZI_LAUNCH_CHECK();
-    ZI_CHECK(launch_dir<T>(p.cptv, dim3(p.g_dir), p.tpr, st, p.n, p.ld, w->alpha, w->beta, R, wpcg, P, X, w->cnt));
+    if constexpr (paired_dir<T>())
+      ZI_CHECK(launch_dir2<T>(odd, p.cptv, dim3(p.g_dir), p.tpr, st, p.n, p.ld, w->alpha, w->alpha2, w->beta, R,
+                              wpcg, Pc, P, P2, X, w->cnt, cs.freeze, (!odd && k == chunk - 1 && flush_last) ? 1 : 0));
+    else
+      ZI_CHECK(launch_dir<T>(p.cptv, dim3(p.g_dir), p.tpr, st, p.n, p.ld, w->alpha, w->beta, R, wpcg, P, X, w->cnt));
   }
   return ZI_OK;
 }
 
 template <typename T>
-static int get_graph(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, T* P, T* Q, int chunk,
+static int get_graph(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, T* P, T* P2, T* Q, int chunk,
                      cudaGraphExec_t* exec, int* have_chunk) {
   if (*exec && *have_chunk == chunk) return ZI_OK;
   if (*exec) {
@@ -1518,7 +1657,7 @@ static int get_graph(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* 
   cudaGraph_t g;
   ZI_CUDA(cudaStreamBeginCapture(w->stream, cudaStreamCaptureModeThreadLocal));
   g_capturing = true;
-  int st = record_iterations<T>(p, w, vals, X, R, P, Q, chunk, w->stream);
+  int st = record_iterations<T>(p, w, vals, X, R, P, P2, Q, chunk, w->stream);
   g_capturing = false;
   cudaError_t e = cudaStreamEndCapture(w->stream, &g);
   if (st != ZI_OK) {
@@ -1537,15 +1676,28 @@ static int get_graph(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* 
 // iterations have run.  Column state must be initialised.  Returns the
 // number of iterations run through *ran.
 template <typename T>
-static int run_cg(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, T* P, T* Q, int maxit, int chunk,
-                  cudaGraphExec_t* exec, int* have_chunk, int* ran) {
-  ZI_CHECK(get_graph<T>(p, w, vals, X, R, P, Q, chunk, exec, have_chunk));
+static int run_cg(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, T* P, T* P2, T* Q, int maxit,
+                  int chunk, cudaGraphExec_t* exec, int* have_chunk, int* ran) {
+  constexpr bool paired = paired_dir<T>();
+  if (paired) chunk += chunk & 1;  // replays of even length: every replay starts with the direction in P
+  ZI_CHECK(get_graph<T>(p, w, vals, X, R, P, P2, Q, chunk, exec, have_chunk));
+  int it0 = 0;  // iterations of this phase before this run
+  if (paired) {
+    ZI_CUDA(cudaMemcpyAsync(&it0, w->cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, w->stream));
+    ZI_CUDA(cudaStreamSynchronize(w->stream));
+  }
   int done = 0;
   int hcnt[5] = {1, 0, 0, 0, 0};
   while (done < maxit) {
-    ZI_CUDA(cudaGraphLaunch(*exec, w->stream));
-    count_launches(5 * (int64_t)chunk);  // kernel nodes per iteration
-    done += chunk;
+    if (paired && maxit - done < chunk) {
+      // fewer iterations left than a replay: launched directly, so the bound holds exactly
+      ZI_CHECK(record_iterations<T>(p, w, vals, X, R, P, P2, Q, maxit - done, w->stream, true));
+      done = maxit;
+    } else {
+      ZI_CUDA(cudaGraphLaunch(*exec, w->stream));
+      count_launches(5 * (int64_t)chunk);  // kernel nodes per iteration
+      done += chunk;
+    }
     ZI_CUDA(cudaMemcpyAsync(hcnt, w->cnt, 5 * sizeof(int), cudaMemcpyDeviceToHost, w->stream));
     ZI_CUDA(cudaStreamSynchronize(w->stream));
     if (hcnt[4]) {
@@ -1555,6 +1707,8 @@ static int run_cg(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, 
     if (hcnt[0] == 0 || hcnt[2] > 0) break;
   }
   *ran = hcnt[1];  // iterations that ran; the rest of the last chunk returned at once
+  if (paired && ((hcnt[1] - it0) & 1))  // the run ended on an even iteration: the current direction is in P2
+    ZI_CUDA(cudaMemcpyAsync(P, P2, sizeof(T) * (size_t)p.n * p.ld, cudaMemcpyDeviceToDevice, w->stream));
   return ZI_OK;
 }
 
@@ -1599,6 +1753,7 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
     ZI_CHECK(dalloc_n(&w->part2, (size_t)w->nblk * ld, s));
     ZI_CHECK(dalloc_n(&w->rho, ld, s));
     ZI_CHECK(dalloc_n(&w->alpha, ld, s));
+    ZI_CHECK(dalloc_n(&w->alpha2, ld, s));
     ZI_CHECK(dalloc_n(&w->beta, ld, s));
     ZI_CHECK(dalloc_n(&w->stop2, ld, s));
     ZI_CHECK(dalloc_n(&w->bb, ld, s));
@@ -1622,6 +1777,7 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
     ZI_CHECK(dalloc_n(&w->r32, nl, s));
     ZI_CHECK(dalloc_n(&w->p32, nl, s));
     ZI_CHECK(dalloc_n(&w->q32, nl, s));
+    ZI_CHECK(dalloc_n(&w->p32b, nl, s));
     w->v32_ready = false;
   }
   if (!S->T) ZI_CHECK(dalloc_n(&S->T, S->n * (int64_t)S->n_rhs, s));
@@ -2055,13 +2211,13 @@ static int run_inner(HeadRun& h, int maxit, int chunk, int* ran) {
   if (h.mixed) {
     double* dtrue_saved = w->dtrue;
     w->dtrue = w->w32;
-    int st2 = run_cg<float>(h.p32, w, w->v32, w->x32, w->r32, w->p32, w->q32, maxit, chunk, &w->graph32,
+    int st2 = run_cg<float>(h.p32, w, w->v32, w->x32, w->r32, w->p32, w->p32b, w->q32, maxit, chunk, &w->graph32,
                             &w->graph_chunk32, ran);
     w->dtrue = dtrue_saved;
     return st2;
   }
-  return run_cg<double>(h.p64, w, w->v64, w->X, w->R, w->P, w->Q, maxit, chunk, &w->graph64, &w->graph_chunk64,
-                        ran);
+  return run_cg<double>(h.p64, w, w->v64, w->X, w->R, w->P, nullptr, w->Q, maxit, chunk, &w->graph64,
+                        &w->graph_chunk64, ran);
 }
 
 int transfer_impl(zi_system* S, const zi_solver_opts* o, double* Tout, int32_t* iters, double* relres,

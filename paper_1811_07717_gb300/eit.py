@@ -25,8 +25,7 @@ class EITVoltages(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, log_s, system, sigma_base6, I, opts):
-        s6 = (sigma_base6 * torch.exp(log_s.detach())[:, None]).contiguous()
-        system.set_conductivity(s6)
+        system.set_log_conductivity(sigma_base6, log_s.detach())
         system.transfer(opts, want_T=False)
         y, _ = system.eit(I, mode=None, opts=opts)
         ctx.system = system

@@ -28,7 +28,8 @@ STENCIL_WIDTH = 8
 
 # Every symbol include/zi.h declares.
 EXPORTS = ("zi_version", "zi_last_error", "zi_status_string", "zi_mesh_from_grid", "zi_locate_dipoles_grid",
-           "zi_mesh_from_surfaces", "zi_nearest_source", "zi_locate_points", "zi_leadfield_at", "zi_assemble", "zi_system_set_conductivity",
+           "zi_mesh_from_surfaces", "zi_nearest_source", "zi_locate_points", "zi_leadfield_at",
+           "zi_system_set_log_conductivity", "zi_assemble", "zi_system_set_conductivity",
            "zi_system_get_info", "zi_system_get_matrix", "zi_system_destroy", "zi_solver_opts_default",
            "zi_transfer", "zi_transfer_batched", "zi_leadfield", "zi_source_stencil", "zi_leadfield_sparse",
            "zi_source_pi", "zi_meg_rhs", "zi_meg_transfer", "zi_meg_leadfield", "zi_eit_jacobian",
@@ -109,6 +110,7 @@ def load_library(path: str = LIB_PATH):
         "zi_mesh_from_surfaces": ([D, ctypes.c_int, P, P, P, I64, P, P, P, P, P, P, P, P, P], ctypes.c_int),
         "zi_assemble": ([P, I64, P, I64, P, P, I64, ctypes.POINTER(_Electrodes), P, P], ctypes.c_int),
         "zi_system_set_conductivity": ([P, P, P], ctypes.c_int),
+        "zi_system_set_log_conductivity": ([P, P, P, P], ctypes.c_int),
         "zi_system_get_info": ([P, ctypes.POINTER(_Info)], ctypes.c_int),
         "zi_system_get_matrix": ([P, P, P, P, P, P, P, P], ctypes.c_int),
         "zi_system_destroy": ([P], None),
@@ -380,6 +382,16 @@ class System:
         s6 = _dev(sigma6, torch.float64)
         _check(self._lib.zi_system_set_conductivity(self._h, _ptr(s6), _stream()))
         self.sigma6 = s6
+        self.version += 1
+
+    def set_log_conductivity(self, sigma_base6, log_s):
+        """Element tensors exp(log_s[e]) * sigma_base6[e], formed and assembled in
+        libzi (zi_system_set_log_conductivity)."""
+        torch = _torch()
+        base = _dev(sigma_base6, torch.float64, self.nodes.device).contiguous()
+        ls = _dev(log_s, torch.float64, self.nodes.device).contiguous()
+        _check(self._lib.zi_system_set_log_conductivity(self._h, _ptr(base), _ptr(ls), _stream()))
+        self.sigma6 = None
         self.version += 1
 
     def transfer(self, opts: SolverOpts | None = None, want_T: bool = True, allow_not_converged=False):

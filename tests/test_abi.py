@@ -80,6 +80,7 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.zi_apply_operator(None, ctypes.byref(o), None, None, None, None) == zi.ZI_ERR_ARG
     assert lib.zi_solver_get_info(None, None) == zi.ZI_ERR_ARG
     assert lib.zi_locate_points(None, 0, None, 0, None, 1, None, None) == zi.ZI_ERR_ARG
+    assert lib.zi_system_set_log_conductivity(None, None, None, None) == zi.ZI_ERR_ARG
     assert lib.zi_leadfield_at(None, None, 1, ctypes.byref(o), None, None) == zi.ZI_ERR_ARG
     assert lib.zi_batch_tune(None, 0, ctypes.byref(o), None, None, None) == zi.ZI_ERR_ARG
     assert lib.zi_transfer_batched_schedule(None, 0, ctypes.byref(o), None, None, None, 0, None) == zi.ZI_ERR_ARG

@@ -122,3 +122,20 @@ def test_full_size_eit_sum_rule_and_vjp_consistency():
     yh = y.cpu().numpy()
     assert np.linalg.norm(Jsum + dz + yh) <= 1e-6 * np.linalg.norm(yh)
     system.close()
+
+
+def test_log_conductivity_is_formed_in_the_library():
+    """zi_system_set_log_conductivity assembles the same matrix as
+    zi_system_set_conductivity of exp(log_s) * base (the EIT parametrisation
+    is applied in libzi, not in torch)."""
+    spec = W.unit_sphere_cem(h=0.2, n_electrodes=16)
+    mesh, s6, centres, z, system = _setup(spec)
+    m = mesh["tets"].shape[0]
+    base = torch.from_numpy(s6).cuda()
+    log_s = torch.from_numpy(np.random.default_rng(4).normal(0.0, 0.3, m)).cuda()
+    system.set_log_conductivity(base, log_s)
+    a = system.matrix()[2].cpu().numpy()
+    system.set_conductivity((base * torch.exp(log_s)[:, None]).contiguous())
+    b = system.matrix()[2].cpu().numpy()
+    assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(b))
+    system.close()
