@@ -309,20 +309,27 @@ def measured_peak_gbs():
 
 
 def spmm_source_sha():
-    """Hash of the source the FP32 ELL SpMM is compiled from: the shared
-    header and zi_pcg.cu from its first include to the end of k_spmm_ell
-    (the file's leading comment and everything after the kernel -- the vector
-    kernels, the batched kernel, the host code -- cannot change the SpMM's
-    code)."""
+    """Hash of the source that decides the FP32 ELL SpMM's code and its memory
+    traffic: the shared header, zi_pcg.cu from its first include to the end
+    of k_spmm_ell, and the code that chooses the copy's storage order (the
+    tile kernels and ell_order).  The file's leading comment, the vector
+    kernels, the batched kernel and the rest of the host code change
+    neither."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1811_07717_gb300", "csrc")
     with open(os.path.join(csrc, "zi_internal.cuh"), "rb") as f:
         head = f.read()
     with open(os.path.join(csrc, "zi_pcg.cu"), "rb") as f:
         body = f.read()
-    start = max(body.find(b"#include"), 0)
-    end = body.find(b"// r -= alpha q, with the column partials")
-    return hashlib.sha256(head + (body[start:end] if end > 0 else body[start:])).hexdigest()[:16]
+
+    def part(a, b):
+        i = body.find(a)
+        j = body.find(b, i + 1) if i >= 0 else -1
+        return body[i:j] if i >= 0 and j > i else b""
+    kernel = part(b"#include", b"// r -= alpha q, with the column partials")
+    order = part(b"// Storage order of the FP32 ELL copy.", b"// Builds the padded, scaled right-hand side")
+    order_host = part(b"// Storage position of every row of the FP32 ELL copy", b"// Scaled FP64 matrix, and the FP32")
+    return hashlib.sha256(head + kernel + order + order_host).hexdigest()[:16]
 
 
 # ---------------------------------------------------------------------------

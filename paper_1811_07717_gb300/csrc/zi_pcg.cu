@@ -974,8 +974,9 @@ __global__ void k_fill_ell(int64_t n, const int32_t* __restrict__ rowptr32, cons
 // In-tile neighbours are then at most ORD_TX * ORD_TY rows apart, y-tile
 // neighbours one tile column apart, and only the x-faces of the tiles (2 rows
 // in ORD_TX) reach further.  The vectors stay in mesh order; the SpMM takes
-// each row's index from its slot 0.
-constexpr int ORD_TX = 16, ORD_TY = 8;
+// each row's index from its slot 0.  8 x 4 won a sweep of 2x2 .. 64x8 on the
+// 1 mm head (a tile layer is then one 32-row staging chunk at 256 columns).
+constexpr int ORD_TX = 8, ORD_TY = 4;
 
 __device__ __forceinline__ unsigned long long ord_key(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
