@@ -52,7 +52,7 @@ DEFAULT_WORKLOAD = "aniso1mm"
 SPMM_TRAFFIC = {
     "shell2mm": {"source_sha": "773b0a3cd13d3b2b", "bytes": 246.967552e6 + 184.626944e6,
                  "note": "one ncu capture (--set full) of the standalone launch on this workload"},
-    "aniso1mm": {"source_sha": "773b0a3cd13d3b2b", "bytes": 5.33e9 + 3.39e9,
+    "aniso1mm": {"source_sha": "374b333020ff7dd2", "bytes": 5.44e9 + 3.39e9,
                  "note": "one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the "
                          "standalone launch on this workload at full size"},
 }

@@ -1727,6 +1727,8 @@ static int ensure_scratch(zi_system* S, const zi_solver_opts* o, cudaStream_t s)
   if (!w) {
     int ld, c64, c32;
     choose_layout(S->n_rhs, &ld, &c64, &c32);
+    // every CG kernel keeps one shared-memory total per column (MAX_LD of them)
+    if (ld > MAX_LD) return set_error(ZI_ERR_ARG, "more than %d right-hand sides per system", MAX_LD);
     int64_t nl = S->n * (int64_t)ld;
     // vector offsets (row * ld / 2 for FP64 16-byte vectors) are 32-bit in the CG kernels
     if (nl / 2 > (int64_t)INT32_MAX)

@@ -11,7 +11,8 @@ the oracle's assembled A:
   plus the couplings the FP32 copy leaves to c_i (|a_ij| <= 2^-24 sqrt(a_ii a_jj));
 * the fused dots against FP64 host sums of the same x and y;
 at 32, 128 and 256 right-hand sides on an anisotropic-skull head whose rows
-overflow the eight ELL slots (the layout is asserted)."""
+overflow the eight ELL slots (the layout is asserted).  More than 256
+right-hand sides are refused before any solver launch."""
 import numpy as np
 import pytest
 
@@ -27,6 +28,11 @@ if not torch.cuda.is_available():
 from paper_1811_07717_gb300 import zi  # noqa: E402
 
 U32 = 2.0 ** -24
+# right-hand sides and electrode radii (6 mm head), with the FP64 layout each
+# gets: one, two or four 16-byte vectors of a row per thread
+SIZES = [(32, 0.009), (128, 0.006), (256, 0.005)]
+SIZE_IDS = ["ld32", "ld128", "ld256"]
+VECTORS64 = {32: 1, 128: 2, 256: 4}
 
 
 def head(L, radius):
@@ -56,7 +62,7 @@ def noise_mask(A, cut):
     return (rows != A.indices) & (np.abs(A.data) <= cut * np.sqrt(d[rows] * d[A.indices])), rows
 
 
-@pytest.mark.parametrize("L,radius", [(32, 0.009), (128, 0.006), (256, 0.005)], ids=["ld32", "ld128", "ld256"])
+@pytest.mark.parametrize("L,radius", SIZES, ids=SIZE_IDS)
 def test_fp64_operator_and_dots(L, radius):
     gs, A = head(L, radius)
     n = A.shape[0]
@@ -75,13 +81,15 @@ def test_fp64_operator_and_dots(L, radius):
     assert np.all(np.abs(Y - ref) <= tol)
     inf = gs.solver_info()
     assert inf["ld"] == L and inf["nnz64"] == A.nnz - int(mask.sum())
+    assert inf["vectors_per_thread64"] == VECTORS64[L]
+    assert inf["threads_per_row64"] * inf["vectors_per_thread64"] * 2 == L
     host = np.einsum("ic,ic->c", X, Y)
     assert np.all(np.abs(dots - host) <= 1e-12 * np.einsum("ic,ic->c", np.abs(X), np.abs(Y)))
     gs.close()
 
 
 @pytest.mark.parametrize("order", ["rows", "tiles"])
-@pytest.mark.parametrize("L,radius", [(32, 0.009), (128, 0.006), (256, 0.005)], ids=["ld32", "ld128", "ld256"])
+@pytest.mark.parametrize("L,radius", SIZES, ids=SIZE_IDS)
 def test_fp32_difference_form_operator_and_dots(L, radius, order, monkeypatch):
     """Both storage orders of the FP32 ELL copy (row order, and the tile
     columns used on large grids) give the same operator."""
@@ -107,11 +115,34 @@ def test_fp32_difference_form_operator_and_dots(L, radius, order, monkeypatch):
     inf = gs.solver_info()
     assert inf["spmm32"] == zi.SPMM32_ELL_OVERFLOW          # anisotropic rows overflow the 8 slots
     assert inf["ell_tiled"] == (order == "tiles")
+    assert inf["vectors_per_thread32"] == 1
+    assert inf["threads_per_row32"] * 4 == L
     kept_len = np.bincount(rows[~mask], minlength=n)
     assert inf["nnz32"] == int(kept_len.sum())
     assert inf["tail_rows"] == int((kept_len > 8).sum()) and inf["tail_rows"] * 20 > n
     host = np.einsum("ic,ic->c", x32, Y)
     assert np.all(np.abs(dots - host) <= 1e-5 * np.einsum("ic,ic->c", np.abs(x32), np.abs(Y)))
+    gs.close()
+
+
+def test_more_than_256_right_hand_sides_refused():
+    """The solver keeps one shared-memory total per column, 256 at most: a
+    320-electrode system is refused by the operator and the transfer solve
+    before any solver kernel runs (and the SpMM timer finds no solver state)."""
+    spec = W.three_shell(0.006, 320, 10, seed=21, electrode_radius=0.0045)
+    mesh = zi.mesh_from_grid(spec.h, spec.radii)
+    s6 = W.conductivity(spec, *(mesh[k].cpu().numpy() for k in ("nodes", "tets", "labels")))
+    centres, z = W.electrode_inputs(spec)
+    gs = zi.System(mesh["nodes"], mesh["tets"], s6, mesh["bfaces"], centres, model="cem", z=z,
+                   radius=spec.electrode_radius)
+    n = mesh["nodes"].shape[0]
+    for prec in (zi.FP64, zi.MIXED):
+        with pytest.raises(zi.ZiError, match="right-hand sides"):
+            gs.apply_operator(np.zeros((n, 320)), zi.SolverOpts(precision=prec))
+        with pytest.raises(zi.ZiError):                     # no solver state was ever built
+            gs.time_spmm(prec, reps=1)
+        with pytest.raises(zi.ZiError, match="right-hand sides"):
+            gs.transfer(zi.SolverOpts(tol=1e-8, precision=prec), want_T=False)
     gs.close()
 
 
