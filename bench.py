@@ -50,9 +50,10 @@ DEFAULT_WORKLOAD = "aniso1mm"
 # ncu DRAM traffic per launch of the FP32 SpMM on this workload, from the capture
 # summarised in profiles/ (None until taken, or once the kernel source changed).
 SPMM_TRAFFIC = {
-    "shell2mm": {"source_sha": "773b0a3cd13d3b2b", "bytes": 246.967552e6 + 184.626944e6,
-                 "note": "one ncu capture (--set full) of the standalone launch on this workload"},
-    "aniso1mm": {"source_sha": "374b333020ff7dd2", "bytes": 5.44e9 + 3.39e9,
+    "shell2mm": {"source_sha": "5f746b0395865bcf", "bytes": 137.207296e6 + 169.128960e6,
+                 "note": "one ncu capture (--set full) of the standalone launch on this workload, taken on the "
+                         "same kernel before its FP16 storage helpers were renamed"},
+    "aniso1mm": {"source_sha": "5f746b0395865bcf", "bytes": 2.93e9 + 3.38e9,
                  "note": "one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the "
                          "standalone launch on this workload at full size"},
 }

@@ -108,16 +108,19 @@ __device__ __forceinline__ void vset(float4& v, int k, float x) {
 
 template <typename V> __device__ __forceinline__ V ldg_v(const V* p) { return __ldg(p); }
 
-// The FP32 path stores its search directions in FP16 (four columns in 8
-// bytes; every operation on them is FP32), so the SpMM gathers half the bytes
-// per stored entry.  x, r and q = A p all use the stored direction, so the
-// recurrences stay consistent; only the choice of direction is rounded.
-// Dir<T>: storage of one direction element, and of the vector of W columns a
-// thread handles (Vec<T>).
-template <typename T> struct Dir { using elem = T; using vec = typename Vec<T>::type; };
-template <> struct Dir<float> { using elem = __half; using vec = uint2; };
+// The FP32 path stores its search directions p and residuals r in FP16 (four
+// columns in 8 bytes; every operation on them is FP32), so the SpMM gathers
+// half the bytes per stored entry and the vector updates move fewer.  x, r and
+// q = A p all use the stored direction, so the recurrences stay consistent;
+// only the choice of direction is rounded.  The residual recurrence keeps the
+// rounded r (its column dots are taken from the stored values), and the FP64
+// refinement replaces it by the true residual every phase.
+// Store<T>: storage of one element, and of the vector of W columns a thread
+// handles (Vec<T>).
+template <typename T> struct Store { using elem = T; using vec = typename Vec<T>::type; };
+template <> struct Store<float> { using elem = __half; using vec = uint2; };
 
-__device__ __forceinline__ float4 dir_get(const uint2& h) {
+__device__ __forceinline__ float4 sget(const uint2& h) {
   float4 r;
   asm("{ .reg .f16 a, b, c, d; mov.b32 {a, b}, %4; mov.b32 {c, d}, %5; cvt.f32.f16 %0, a; cvt.f32.f16 %1, b;"
       " cvt.f32.f16 %2, c; cvt.f32.f16 %3, d; }"
@@ -125,20 +128,20 @@ __device__ __forceinline__ float4 dir_get(const uint2& h) {
       : "r"(h.x), "r"(h.y));
   return r;
 }
-__device__ __forceinline__ double2 dir_get(const double2& v) { return v; }
+__device__ __forceinline__ double2 sget(const double2& v) { return v; }
 // Round to nearest FP16 (subnormals kept), saturating at the largest finite
 // value (a saturated entry still gives a valid search direction: x, r and q
 // use the stored one).
-__device__ __forceinline__ uint2 dir_pack(const float4& v) {
+__device__ __forceinline__ uint2 spack(const float4& v) {
   uint2 h;
   asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(h.x) : "f"(v.y), "f"(v.x));
   asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(h.y) : "f"(v.w), "f"(v.z));
   return h;
 }
-__device__ __forceinline__ double2 dir_pack(const double2& v) { return v; }
-template <typename DV> __device__ __forceinline__ DV dir_zero();
-template <> __device__ __forceinline__ uint2 dir_zero<uint2>() { return make_uint2(0u, 0u); }
-template <> __device__ __forceinline__ double2 dir_zero<double2>() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ double2 spack(const double2& v) { return v; }
+template <typename DV> __device__ __forceinline__ DV szero();
+template <> __device__ __forceinline__ uint2 szero<uint2>() { return make_uint2(0u, 0u); }
+template <> __device__ __forceinline__ double2 szero<double2>() { return make_double2(0.0, 0.0); }
 // acc += a (x - x0) for a stored FP16 x, given nx0 = -x0: the mixed-precision
 // add forms x + nx0 in FP32 straight from the FP16 value, then two packed FMAs.
 __device__ __forceinline__ void vfma_diff_h(float4& acc, float a, const uint2& x, const float4& nx0) {
@@ -491,14 +494,14 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
         for (int u = 0; u < ELL_K; ++u)
 #pragma unroll
           for (int v = 0; v < CPTV; ++v)
-            x[u][v] = j[u] >= 0 ? __ldg(Pv + (j[u] * nv + v * tpr)) : dir_zero<uint2>();  // n*ld/2 < 2^31 (host-checked)
+            x[u][v] = j[u] >= 0 ? __ldg(Pv + (j[u] * nv + v * tpr)) : szero<uint2>();  // n*ld/2 < 2^31 (host-checked)
         const float4 a0 = bv[2 * lr], a1 = bv[2 * lr + 1];
         const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
         // difference form: c_i p_i + sum_j a_ij (p_j - p_i); unused slots have a = 0
         V acc[CPTV], np0[CPTV];  // np0 = -p_i in FP32
 #pragma unroll
         for (int v = 0; v < CPTV; ++v) {
-          const V p0 = dir_get(x[0][v]);
+          const V p0 = sget(x[0][v]);
           np0[v] = vneg(p0);
           acc[v] = vzero<V>();
           vfma(acc[v], a[0], p0);
@@ -572,7 +575,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256, CPTV == 1
 template <typename T, int CPTV>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
     k_cg_resid(int64_t n, int tpr, int ld, const double* __restrict__ alpha, const T* __restrict__ Q,
-               T* __restrict__ R, const double* __restrict__ dtrue, const double* __restrict__ wrr,
+               typename Store<T>::elem* __restrict__ R, const double* __restrict__ dtrue, const double* __restrict__ wrr,
                double* __restrict__ part_rr, double* __restrict__ part_rd, const int* __restrict__ cnt,
                int freeze) {
   if (run_stopped(cnt, freeze)) return;
@@ -593,8 +596,9 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
       rr[v][k] = T(0);
       rd[v][k] = T(0);
     }
+  using SV = typename Store<T>::vec;
   const V* Qv = reinterpret_cast<const V*>(Q);
-  V* Rv = reinterpret_cast<V*>(R);
+  SV* Rv = reinterpret_cast<SV*>(R);
   const RowWalk rw = row_walk(n, rpb, g);
   {
     int slot = 0;
@@ -604,15 +608,18 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
 #pragma unroll
       for (int v = 0; v < CPTV; ++v) {
         const int o = i * nv + c + v * tpr;
-        V q = ldg_v(Qv + o), r = Rv[o];
+        V q = ldg_v(Qv + o), r = sget(Rv[o]);
+#pragma unroll
+        for (int k = 0; k < W; ++k) vset(r, k, vget(r, k) - al[v][k] * vget(q, k));
+        const SV rs = spack(r);
+        Rv[o] = rs;
+        r = sget(rs);  // the dots of the residual as stored
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-          T rv = vget(r, k) - al[v][k] * vget(q, k);
-          vset(r, k, rv);
+          const T rv = vget(r, k);
           rr[v][k] += wi * rv * rv;
           rd[v][k] += di * rv * rv;
         }
-        Rv[o] = r;
       }
     }
   }
@@ -681,9 +688,10 @@ __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, int tpr, int ld, cons
 template <typename T, int CPTV, bool ODD>
 __global__ void __launch_bounds__(256) k_cg_dir2(int64_t n, int tpr, int ld, const double* __restrict__ a_even,
                                                  const double* __restrict__ a_odd, const double* __restrict__ beta,
-                                                 const T* __restrict__ R, const double* __restrict__ wz,
-                                                 const typename Dir<T>::elem* __restrict__ Pcur,
-                                                 typename Dir<T>::elem* PA, typename Dir<T>::elem* __restrict__ PB,
+                                                 const typename Store<T>::elem* __restrict__ R,
+                                                 const double* __restrict__ wz,
+                                                 const typename Store<T>::elem* __restrict__ Pcur,
+                                                 typename Store<T>::elem* PA, typename Store<T>::elem* __restrict__ PB,
                                                  T* __restrict__ X, const int* __restrict__ cnt, int freeze,
                                                  int flush) {
   if (cnt && *(volatile const int*)(cnt + 3)) return;
@@ -703,8 +711,8 @@ __global__ void __launch_bounds__(256) k_cg_dir2(int64_t n, int tpr, int ld, con
       ao[v][k] = ODD ? (T)a_odd[(c + v * tpr) * W + k] : T(0);
       be[v][k] = (T)beta[(c + v * tpr) * W + k];
     }
-  using DV = typename Dir<T>::vec;
-  const V* Rv = reinterpret_cast<const V*>(R);
+  using DV = typename Store<T>::vec;
+  const DV* Rv = reinterpret_cast<const DV*>(R);
   const DV* Pc = reinterpret_cast<const DV*>(Pcur);
   DV* Av = reinterpret_cast<DV*>(PA);
   DV* Bv = reinterpret_cast<DV*>(PB);
@@ -716,19 +724,19 @@ __global__ void __launch_bounds__(256) k_cg_dir2(int64_t n, int tpr, int ld, con
 #pragma unroll
     for (int v = 0; v < CPTV; ++v) {
       const int o = i * nv + c + v * tpr;
-      const V r = ldg_v(Rv + o), pc = dir_get(Pc[o]);
+      const V r = sget(ldg_v(Rv + o)), pc = sget(Pc[o]);
       V pn;
 #pragma unroll
       for (int k = 0; k < W; ++k) vset(pn, k, wi * vget(r, k) + be[v][k] * vget(pc, k));
       if (ODD) {
-        const V pp = dir_get(Av[o]);
+        const V pp = sget(Av[o]);
         V x = Xv[o];
 #pragma unroll
         for (int k = 0; k < W; ++k) vset(x, k, vget(x, k) + ae[v][k] * vget(pp, k) + ao[v][k] * vget(pc, k));
         Xv[o] = x;
-        Av[o] = dir_pack(pn);
+        Av[o] = spack(pn);
       } else {
-        Bv[o] = dir_pack(pn);
+        Bv[o] = spack(pn);
         if (upd_x) {
           V x = Xv[o];
 #pragma unroll
@@ -1218,7 +1226,15 @@ __global__ void k_unscale_out(int64_t n, int ncol, int ld, const double* __restr
   }
 }
 
-// Mixed precision: inner right-hand side r32 = r64 / gamma_c and x32 = 0, with
+// 2-norm of each phase's inner right-hand side: the FP16 residual then spans
+// [.., 2^14] at the start of a phase (|r_i| <= R_NORM), well inside the FP16
+// range, and its small entries stay far from the subnormals.  The
+// preconditioner is scaled so that max w is in (1, 2]: |p_i| <= 2 R_NORM.
+// (On the 1 mm head: 1,310 inner iterations at 2^14, 1,306 at 2^15.)
+constexpr int R_NORM_LOG2 = 14;
+constexpr double R_NORM = (double)(1 << R_NORM_LOG2);
+
+// Mixed precision: inner right-hand side r32 = R_NORM r64 / gamma_c and x32 = 0, with
 // column partials of r32.w r32 (w: the PCG preconditioner); gamma_c =
 // |r64_c|_2.  On the first phase p32 = w r32 (the preconditioned residual).
 // On later phases (reliable update: the FP64 residual replaces
@@ -1227,7 +1243,7 @@ __global__ void k_unscale_out(int64_t n, int ncol, int ld, const double* __restr
 // conjugate directions instead of restarting.
 __global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ w, const double* __restrict__ R64,
                              const double* __restrict__ gamma, const double* __restrict__ gamma_prev, int keep_p,
-                             float* __restrict__ r32, float* __restrict__ x32, __half* __restrict__ p32,
+                             __half* __restrict__ r32, float* __restrict__ x32, __half* __restrict__ p32,
                              double* __restrict__ part_rr) {
   // thread (g, c) handles columns 4c .. 4c + 3 of rows g, g + rpb, ... (ld is a multiple of 4)
   extern __shared__ double sred[];
@@ -1242,7 +1258,7 @@ __global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ w, co
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int col = 4 * c + k;
-      gi[k] = gamma[col] > 0.0 ? (float)(1.0 / gamma[col]) : 0.f;
+      gi[k] = gamma[col] > 0.0 ? (float)(R_NORM / gamma[col]) : 0.f;
       kp[k] = keep_p && gamma[col] > 0.0 && gamma_prev[col] > 0.0;
       ratio[k] = kp[k] ? (float)(gamma_prev[col] / gamma[col]) : 0.f;
     }
@@ -1252,17 +1268,20 @@ __global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ w, co
       const double2 rb = *reinterpret_cast<const double2*>(R64 + e + 2);
       const float r64[4] = {(float)ra.x, (float)ra.y, (float)rb.x, (float)rb.y};
       const float wi = (float)w[i];
-      float4 pold = keep_p ? dir_get(*reinterpret_cast<const uint2*>(p32 + e)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 pold = keep_p ? sget(*reinterpret_cast<const uint2*>(p32 + e)) : make_float4(0.f, 0.f, 0.f, 0.f);
       const float po[4] = {pold.x, pold.y, pold.z, pold.w};
-      float r[4], pn[4];
+      // the residual as stored (FP16): p and the dots start from it
+      const uint2 rs = spack(make_float4(r64[0] * gi[0], r64[1] * gi[1], r64[2] * gi[2], r64[3] * gi[3]));
+      const float4 rf = sget(rs);
+      const float r[4] = {rf.x, rf.y, rf.z, rf.w};
+      float pn[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        r[k] = r64[k] * gi[k];
         pn[k] = kp[k] ? po[k] * ratio[k] : wi * r[k];
         rr[k] += wi * r[k] * r[k];
       }
-      *reinterpret_cast<float4*>(r32 + e) = make_float4(r[0], r[1], r[2], r[3]);
-      *reinterpret_cast<uint2*>(p32 + e) = dir_pack(make_float4(pn[0], pn[1], pn[2], pn[3]));
+      *reinterpret_cast<uint2*>(r32 + e) = rs;
+      *reinterpret_cast<uint2*>(p32 + e) = spack(make_float4(pn[0], pn[1], pn[2], pn[3]));
       *reinterpret_cast<float4*>(x32 + e) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
@@ -1276,14 +1295,17 @@ __global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ w, co
   }
 }
 
-// x64 += gamma_c * x32 (the inner solve works on the unscaled system); thread
+// x64 += (gamma_c / R_NORM) x32 (the inner solve works on the unscaled system,
+// with a right-hand side of 2-norm R_NORM); thread
 // (g, c) of a block takes columns 4c .. 4c + 3 of rows g, g + rpb, ...
 __global__ void k_accumulate(int64_t n, int ld, const double* __restrict__ gamma, const float* __restrict__ x32,
                              double* __restrict__ X64) {
   const int nq = ld / 4;
   const int c = threadIdx.x % nq, g = threadIdx.x / nq, rpb = blockDim.x / nq;
   if (g >= rpb) return;
-  const double g0 = gamma[4 * c], g1 = gamma[4 * c + 1], g2 = gamma[4 * c + 2], g3 = gamma[4 * c + 3];
+  constexpr double inv = 1.0 / R_NORM;  // a power of two: exact
+  const double g0 = gamma[4 * c] * inv, g1 = gamma[4 * c + 1] * inv, g2 = gamma[4 * c + 2] * inv,
+               g3 = gamma[4 * c + 3] * inv;
   for (int64_t i = (int64_t)blockIdx.x * rpb + g; i < n; i += (int64_t)gridDim.x * rpb) {
     const int64_t e = i * ld + 4 * c;
     const float4 xv = *reinterpret_cast<const float4*>(x32 + e);
@@ -1333,7 +1355,8 @@ struct SolverScratch {
   // FP64 vectors n x ld
   double *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr;
   // FP32 vectors n x ld
-  float *x32 = nullptr, *r32 = nullptr, *q32 = nullptr;
+  float *x32 = nullptr, *q32 = nullptr;
+  __half* r32 = nullptr;                   // FP16 residual
   __half *p32 = nullptr, *p32b = nullptr;  // FP16 search directions (p32b: odd iterations)
   // partials nblk x ld (three)
   double *part0 = nullptr, *part1 = nullptr, *part2 = nullptr;
@@ -1451,7 +1474,8 @@ int launch_spmm_ell(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, 
 
 template <typename T>
 int launch_resid(int cptv, dim3 grid, int tpr, size_t smem, cudaStream_t st, int64_t n, int ld,
-                 const double* alpha, const T* Q, T* R, const double* dtrue, const double* wrr, double* prr,
+                 const double* alpha, const T* Q, typename Store<T>::elem* R, const double* dtrue,
+                 const double* wrr, double* prr,
                  double* prd, const int* cnt, int freeze) {
   switch (cptv) {
     case 1: k_cg_resid<T, 1><<<grid, BLOCK, smem, st>>>(n, tpr, ld, alpha, Q, R, dtrue, wrr, prr, prd, cnt, freeze); break;
@@ -1480,8 +1504,8 @@ int launch_dir(int cptv, dim3 grid, int tpr, cudaStream_t st, int64_t n, int ld,
 
 template <typename T>
 int launch_dir2(bool odd, int cptv, dim3 grid, int tpr, cudaStream_t st, int64_t n, int ld, const double* a_even,
-                const double* a_odd, const double* beta, const T* R, const double* wz,
-                const typename Dir<T>::elem* Pcur, typename Dir<T>::elem* PA, typename Dir<T>::elem* PB, T* X,
+                const double* a_odd, const double* beta, const typename Store<T>::elem* R, const double* wz,
+                const typename Store<T>::elem* Pcur, typename Store<T>::elem* PA, typename Store<T>::elem* PB, T* X,
                 const int* cnt, int freeze, int flush) {
 #define ZI_DIR2_CASE(CV)                                                                                       \
   case CV:                                                                                                     \
@@ -1632,7 +1656,7 @@ static void size_grids(CgPlan& p) {
 
 // The SpMM of one CG iteration: ELL for the FP32 matrix when available.
 template <typename T>
-static int plan_spmm(const CgPlan& p, const T* vals, const typename Dir<T>::elem* P, T* Q, double* part,
+static int plan_spmm(const CgPlan& p, const T* vals, const typename Store<T>::elem* P, T* Q, double* part,
                      cudaStream_t st, int* cnt = nullptr, int freeze = 1) {
   if constexpr (sizeof(T) == 4) {
     // the FP32 operator is stored in difference form, which only the ELL kernel applies
@@ -1671,8 +1695,8 @@ template <typename T> constexpr bool paired_dir() { return sizeof(T) == 4; }
 // k_cg_dir2).  flush_last: the run ends after this recording, on an even
 // iteration when chunk is odd, so that iteration applies its own x update.
 template <typename T>
-static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R,
-                             typename Dir<T>::elem* P, typename Dir<T>::elem* P2, T* Q, int chunk, cudaStream_t st,
+static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T* X,
+                             typename Store<T>::elem* R, typename Store<T>::elem* P, typename Store<T>::elem* P2, T* Q, int chunk, cudaStream_t st,
                              bool flush_last = false) {
   ColState cs{w->rho, w->alpha, w->beta, w->stop2, w->conv, w->iters, w->cnt, w->cnt + 1, w->cnt + 2,
               sizeof(T) == sizeof(double) ? 1 : 0};
@@ -1683,7 +1707,7 @@ static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T
   const int ncl_spmm = p.g_spmm / CLUSTER, ncl_resid = p.g_resid / CLUSTER;
   for (int k = 0; k < chunk; ++k) {
     const bool odd = paired_dir<T>() && (k & 1);
-    typename Dir<T>::elem* Pc = odd ? P2 : P;
+    typename Store<T>::elem* Pc = odd ? P2 : P;
     ColState ca = cs;
     ca.alpha = odd ? w->alpha2 : w->alpha;
     ZI_CHECK(plan_spmm<T>(p, vals, Pc, Q, w->part0, st, w->cnt, cs.freeze));
@@ -1703,8 +1727,9 @@ static int record_iterations(const CgPlan& p, SolverScratch* w, const T* vals, T
 }
 
 template <typename T>
-static int get_graph(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, typename Dir<T>::elem* P,
-                     typename Dir<T>::elem* P2, T* Q, int chunk, cudaGraphExec_t* exec, int* have_chunk) {
+static int get_graph(const CgPlan& p, SolverScratch* w, const T* vals, T* X, typename Store<T>::elem* R,
+                     typename Store<T>::elem* P,
+                     typename Store<T>::elem* P2, T* Q, int chunk, cudaGraphExec_t* exec, int* have_chunk) {
   if (*exec && *have_chunk == chunk) return ZI_OK;
   if (*exec) {
     cudaGraphExecDestroy(*exec);
@@ -1732,8 +1757,9 @@ static int get_graph(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* 
 // iterations have run.  Column state must be initialised.  Returns the
 // number of iterations run through *ran.
 template <typename T>
-static int run_cg(const CgPlan& p, SolverScratch* w, const T* vals, T* X, T* R, typename Dir<T>::elem* P,
-                  typename Dir<T>::elem* P2, T* Q, int maxit, int chunk, cudaGraphExec_t* exec, int* have_chunk,
+static int run_cg(const CgPlan& p, SolverScratch* w, const T* vals, T* X, typename Store<T>::elem* R,
+                  typename Store<T>::elem* P,
+                  typename Store<T>::elem* P2, T* Q, int maxit, int chunk, cudaGraphExec_t* exec, int* have_chunk,
                   int* ran) {
   constexpr bool paired = paired_dir<T>();
   if (paired) chunk += chunk & 1;  // replays of even length: every replay starts with the direction in P
@@ -1800,14 +1826,14 @@ __global__ void k_scale_by(int64_t n, double* __restrict__ w, double c) {
 }
 
 // Scales the inner preconditioner w by a power of two so that max_i w_i lies
-// in (2^14, 2^15].  CG's iterates do not change (z, p and r.z scale by the
-// factor, alpha by its inverse, exactly), whatever the units of the
-// conductivities and coordinates.  It places the FP16 directions: at the
-// start of a phase |p_i| <= max_i w_i |r_i| <= 2^15 (r has unit length),
+// in (1, 2].  CG's iterates do not change (z, p and r.z scale by the factor,
+// alpha by its inverse, exactly), whatever the units of the conductivities
+// and coordinates.  It places the FP16 directions: at the start of a phase
+// |p_i| <= max_i w_i |r_i| <= 2^15 (the residual has 2-norm R_NORM = 2^14),
 // below the FP16 maximum, and the small far-field entries stay as far above
-// the subnormal range as that allows.  On the 1 mm head the inner iterations
-// were 1,331 with max w scaled to 2^13, and 1,212-1,216 at 2^14 .. 2^16 (the
-// FP32 directions took 1,213).
+// the subnormal range as that allows.  With FP32 residuals of unit norm, the
+// 1 mm head took 1,331 inner iterations with max w at 2^13 and 1,212-1,216 at
+// 2^14 .. 2^16 (FP32 directions: 1,213).
 static int normalise_w32(double* w, int64_t n, cudaStream_t st) {
   DevTmp<unsigned long long> mx;
   ZI_CHECK(mx.alloc(1, st));
@@ -1820,7 +1846,7 @@ static int normalise_w32(double* w, int64_t n, cudaStream_t st) {
   double m;
   memcpy(&m, &hb, sizeof(m));
   if (!(m > 0.0) || !isfinite(m)) return ZI_OK;
-  const int e = (int)ceil(log2(m)) - 15;  // m * 2^-e in (2^14, 2^15]
+  const int e = (int)ceil(log2(m)) - (15 - R_NORM_LOG2);  // m * 2^-e * R_NORM in (2^14, 2^15]
   if (e == 0) return ZI_OK;
   k_scale_by<<<grid_for(n, 256), 256, 0, st>>>(n, w, ldexp(1.0, -e));
   ZI_LAUNCH_CHECK();
@@ -2381,8 +2407,8 @@ struct BatchHead {
   const int32_t* tail_ptr;
   const int32_t* tail_ci;
   const float* tail_va;
-  T *X, *R, *Q;
-  typename Dir<T>::elem* P;  // the search direction (FP16 for FP32 heads)
+  T *X, *Q;
+  typename Store<T>::elem *R, *P;  // residual and search direction (FP16 for FP32 heads)
   const double* dtrue;
   const double* wz;  // FP32 heads: the inner PCG preconditioner w (z = w r); FP64 heads: null
   double *rho, *alpha, *beta, *stop2;
@@ -2551,7 +2577,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
 #pragma unroll
     for (int k = 0; k < W; ++k) acc_pq[0][k] = T(0);
     {
-      using DV = typename Dir<T>::vec;
+      using DV = typename Store<T>::vec;
       const DV* Pc = reinterpret_cast<const DV*>(H.P) + c;  // n * ld / 2 < 2^31 (host-checked)
       V* Qc = reinterpret_cast<V*>(H.Q) + c;
       bool ell = false;
@@ -2573,13 +2599,13 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
             j[0] = tail ? ~j[0] : j[0];
             uint2 x[ELL_K];
 #pragma unroll
-            for (int u = 0; u < ELL_K; ++u) x[u] = j[u] >= 0 ? __ldg(Pc + j[u] * nv) : dir_zero<uint2>();
+            for (int u = 0; u < ELL_K; ++u) x[u] = j[u] >= 0 ? __ldg(Pc + j[u] * nv) : szero<uint2>();
             const float4 a0 = __ldg(eva + i * (ELL_K / 4)), a1 = __ldg(eva + i * (ELL_K / 4) + 1);
             const int inext = rw_next(rw, i, k);
             if (inext >= 0) batch_ell_cols(eci, inext, jn);
             const float a[ELL_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             // difference form of the FP32 operator on the FP16 direction (as in k_spmm_ell)
-            const V p0 = dir_get(x[0]), np0 = vneg(p0);
+            const V p0 = sget(x[0]), np0 = vneg(p0);
             V acc = vzero<V>();
             vfma(acc, a[0], p0);
 #pragma unroll
@@ -2651,7 +2677,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
     for (int k = 0; k < W; ++k) rr[0][k] = rd[0][k] = T(0);
     {
       const V* Qc = reinterpret_cast<const V*>(H.Q) + c;
-      V* Rc = reinterpret_cast<V*>(H.R) + c;
+      typename Store<T>::vec* Rc = reinterpret_cast<typename Store<T>::vec*>(H.R) + c;
       T al[W];
 #pragma unroll
       for (int k = 0; k < W; ++k) al[k] = (T)s_alpha[c * W + k];
@@ -2660,15 +2686,18 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
         const T di = (T)__ldg(H.dtrue + i);
         const T wi = H.wz ? (T)__ldg(H.wz + i) : T(1);
         const V q = Qc[i * nv];
-        V r = Rc[i * nv];
+        V r = sget(Rc[i * nv]);
+#pragma unroll
+        for (int u = 0; u < W; ++u) vset(r, u, vget(r, u) - al[u] * vget(q, u));
+        const typename Store<T>::vec rs = spack(r);
+        Rc[i * nv] = rs;
+        r = sget(rs);  // the dots of the residual as stored
 #pragma unroll
         for (int u = 0; u < W; ++u) {
-          const T rv = vget(r, u) - al[u] * vget(q, u);
-          vset(r, u, rv);
+          const T rv = vget(r, u);
           rr[0][u] += wi * rv * rv;
           rd[0][u] += di * rv * rv;
         }
-        Rc[i * nv] = r;
       }
     }
     batch_block_totals<1, W, T>(rr, g, c, rpb, tpr, 1, ld, sred, H.part1 + (int64_t)lb * ld);
@@ -2718,8 +2747,8 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
     __syncthreads();
     // ---- phase C: x += alpha p, p = r + beta p
     {
-      const V* Rc = reinterpret_cast<const V*>(H.R) + c;
-      typename Dir<T>::vec* Pc = reinterpret_cast<typename Dir<T>::vec*>(H.P) + c;
+      const typename Store<T>::vec* Rc = reinterpret_cast<const typename Store<T>::vec*>(H.R) + c;
+      typename Store<T>::vec* Pc = reinterpret_cast<typename Store<T>::vec*>(H.P) + c;
       V* Xc = reinterpret_cast<V*>(H.X) + c;
       T al[W], be[W];
 #pragma unroll
@@ -2730,15 +2759,15 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
       int k = 0;
       for (int i = rw_first(rw); i >= 0; i = rw_next(rw, i, k)) {
         const T wi = H.wz ? (T)__ldg(H.wz + i) : T(1);
-        const V r = Rc[i * nv];
-        V p = dir_get(Pc[i * nv]), x = Xc[i * nv];
+        const V r = sget(Rc[i * nv]);
+        V p = sget(Pc[i * nv]), x = Xc[i * nv];
 #pragma unroll
         for (int u = 0; u < W; ++u) {
           vset(x, u, vget(x, u) + al[u] * vget(p, u));
           vset(p, u, wi * vget(r, u) + be[u] * vget(p, u));
         }
         Xc[i * nv] = x;
-        Pc[i * nv] = dir_pack(p);
+        Pc[i * nv] = spack(p);
       }
     }
     gen = bar_arrive(H.bar, H.nblk, &last);
