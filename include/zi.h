@@ -65,8 +65,11 @@ enum { ZI_PRECOND_JACOBI = 0, ZI_PRECOND_LDP = 1 };
  * refinement (FP64 residual b - A x and solution update).  The FP32 solve
  * works on the unscaled matrix in difference form, c_i p_i + sum_j a_ij
  * (p_j - p_i) with c_i the row sum, which avoids the cancellation of the plain
- * stencil on smooth vectors.  Both precisions omit couplings at assembly
- * rounding level (|a_ij| <= 2^-40 sqrt(a_ii a_jj); FP32: <= 2^-24). */
+ * stencil on smooth vectors; it stores its search directions and residuals in
+ * FP16 (round to nearest, saturating) and computes in FP32, with x and A p in
+ * FP32.  The FP64 refinement decides the accuracy in both precisions.  Both
+ * omit couplings at assembly rounding level (|a_ij| <= 2^-40 sqrt(a_ii a_jj);
+ * FP32: <= 2^-24). */
 enum { ZI_FP64 = 0, ZI_MIXED = 1 };
 /* EIT output modes. */
 enum { ZI_EIT_FULL = 0, ZI_EIT_VJP = 1 };
@@ -519,7 +522,8 @@ int zi_ias_map(const double* L, int32_t Le, int64_t n, const double* Y, int32_t 
  * ZI_MIXED (FP32 product).  Requires a prior zi_transfer with the same
  * precision.  Writes the mean launch time in ms to *ms_per_launch and the
  * kernel's algorithmic bytes per launch (matrix values, column indices, row
- * pointers, one read of P and one write of Q) to *bytes_per_launch. */
+ * pointers, one read of P and one write of Q; for ZI_MIXED, P is read in FP16
+ * and Q written in FP32) to *bytes_per_launch. */
 int zi_time_spmm(zi_system* sys, int precision, int reps, double* ms_per_launch,
                  double* bytes_per_launch, cudaStream_t stream);
 
@@ -541,10 +545,11 @@ int zi_time_source_apply(zi_system* sys, const int32_t* F_nodes, const double* F
  *     without its rounding-noise entries (|a_ij| <= 2^-40 sqrt(|a_ii a_jj|)),
  *     S = D^-1/2 with D the diagonal of opts->precond (a_ii for Jacobi,
  *     sum_j |a_ij| for LDP);
- *   ZI_MIXED: Y = A X by the inner FP32 operator: X rounded to FP32, A in
- *     difference form (A x)_i = c_i x_i + sum_{j != i} a_ij (x_j - x_i) with
- *     c_i the FP64 row sum, entries below 2^-24 of the scaled diagonal left to
- *     c_i; FP32 arithmetic.
+ *   ZI_MIXED: Y = A X by the inner FP32 operator: X rounded to FP16 (round to
+ *     nearest even, saturating at +-65504: the storage of the FP32 path's
+ *     search directions), A in difference form (A x)_i = c_i x_i +
+ *     sum_{j != i} a_ij (x_j - x_i) with c_i the FP64 row sum, entries below
+ *     2^-24 of the scaled diagonal left to c_i; FP32 arithmetic.
  *   X: device n x n_rhs f64 (node-major, like T); Y: device out, n x n_rhs f64.
  *   dots: device out, n_rhs f64, or NULL: the column dots sum_i x_ic y_ic as the
  *     CG forms its p.q (per-thread partials, then per-block and per-cluster
