@@ -675,8 +675,9 @@ __global__ void __launch_bounds__(256) k_cg_dir(int64_t n, int tpr, int ld, cons
 }
 
 // The direction update with x applied every second iteration, so that one
-// pass over x serves two iterations (4.5 vector sweeps per iteration on
-// average instead of 5).  The search direction alternates between two
+// pass over x serves two iterations (with every vector in FP32: 4.5 vector
+// sweeps per iteration on average instead of 5; with r and p in FP16, 2.75
+// FP32-vector equivalents).  The search direction alternates between two
 // buffers A (even iterations read it) and B (odd iterations read it):
 //   even k: p_{k+1} = z + beta p_k into B; x += alpha_k p_k at once only when
 //           the run stopped after this iteration or `flush` is set (the last
@@ -1354,7 +1355,7 @@ struct SolverScratch {
   float* tail_va = nullptr;
   // FP64 vectors n x ld
   double *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr;
-  // FP32 vectors n x ld
+  // mixed-path vectors n x ld: x and q in FP32, r and p in FP16
   float *x32 = nullptr, *q32 = nullptr;
   __half* r32 = nullptr;                   // FP16 residual
   __half *p32 = nullptr, *p32b = nullptr;  // FP16 search directions (p32b: odd iterations)
@@ -2239,8 +2240,8 @@ int mixed_phase_begin(HeadRun& h) {
     h.status = set_error(ZI_ERR_NOT_CONVERGED, "mixed-precision refinement missed tol=%g", o->tol);
     return ZI_OK;
   }
-  // inner right-hand side r32 = R64 / |R64|, x32 = 0, p32 = w r32 (kept and
-  // rescaled after the first phase)
+  // inner right-hand side r32 = R_NORM R64 / |R64|, x32 = 0, p32 = w r32 (kept
+  // and rescaled after the first phase)
   const size_t smem_prep = sizeof(double) * (size_t)(BLOCK / (ld / 4)) * ld;  // four columns per thread
   k_prep_inner<<<nblk, BLOCK, smem_prep, st>>>(n, ld, w->w32, w->R, w->gamma, w->gamma_prev, h.outer > 0 ? 1 : 0,
                                                w->r32, w->x32, w->p32, w->part0);
