@@ -2578,6 +2578,8 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
 #pragma unroll
     for (int k = 0; k < W; ++k) acc_pq[0][k] = T(0);
     {
+      // P is rewritten in phase C by other blocks of this launch: plain (coherent) loads, ordered after
+      // the head barrier's fences, not the read-only __ldg path
       using DV = typename Store<T>::vec;
       const DV* Pc = reinterpret_cast<const DV*>(H.P) + c;  // n * ld / 2 < 2^31 (host-checked)
       V* Qc = reinterpret_cast<V*>(H.Q) + c;
@@ -2600,7 +2602,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
             j[0] = tail ? ~j[0] : j[0];
             uint2 x[ELL_K];
 #pragma unroll
-            for (int u = 0; u < ELL_K; ++u) x[u] = j[u] >= 0 ? __ldg(Pc + j[u] * nv) : szero<uint2>();
+            for (int u = 0; u < ELL_K; ++u) x[u] = j[u] >= 0 ? Pc[j[u] * nv] : szero<uint2>();
             const float4 a0 = __ldg(eva + i * (ELL_K / 4)), a1 = __ldg(eva + i * (ELL_K / 4) + 1);
             const int inext = rw_next(rw, i, k);
             if (inext >= 0) batch_ell_cols(eci, inext, jn);
@@ -2615,7 +2617,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
             if (tail) {
               const int t0 = __ldg(H.tail_ptr + j[0]), t1 = __ldg(H.tail_ptr + j[0] + 1);
               for (int t = t0; t < t1; ++t)
-                vfma_diff_h(acc, __ldg(H.tail_va + t), __ldg(Pc + __ldg(H.tail_ci + t) * nv), np0);
+                vfma_diff_h(acc, __ldg(H.tail_va + t), Pc[__ldg(H.tail_ci + t) * nv], np0);
             }
             Qc[j[0] * nv] = acc;
 #pragma unroll
@@ -2639,12 +2641,12 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
             load_batch<T, G>(e, r1, colind, vals, j, a);
             V x[G];
 #pragma unroll
-            for (int u = 0; u < G; ++u) x[u] = j[u] >= 0 ? ldg_v(Pc + j[u] * nv) : vzero<V>();
+            for (int u = 0; u < G; ++u) x[u] = j[u] >= 0 ? Pc[j[u] * nv] : vzero<V>();
 #pragma unroll
             for (int u = 0; u < G; ++u) vfma(acc, a[u], x[u]);
           }
           Qc[i * nv] = acc;
-          const V pv = ldg_v(Pc + i * nv);
+          const V pv = Pc[i * nv];
 #pragma unroll
           for (int kk = 0; kk < W; ++kk) acc_pq[0][kk] += vget(pv, kk) * vget(acc, kk);
         }
