@@ -50,12 +50,14 @@ DEFAULT_WORKLOAD = "aniso1mm"
 # ncu DRAM traffic per launch of the FP32 SpMM on this workload, from the capture
 # summarised in profiles/ (None until taken, or once the kernel source changed).
 SPMM_TRAFFIC = {
-    "shell2mm": {"source_sha": "5f746b0395865bcf", "bytes": 137.207296e6 + 169.128960e6,
+    "shell2mm": {"source_sha": "9b1e26a920e49e63", "bytes": 137.207296e6 + 169.128960e6,
                  "note": "one ncu capture (--set full) of the standalone launch on this workload, taken on the "
-                         "same kernel before its FP16 storage helpers were renamed"},
-    "aniso1mm": {"source_sha": "5f746b0395865bcf", "bytes": 2.93e9 + 3.38e9,
+                         "same kernel code (since then only its FP16 storage helpers were renamed and a "
+                         "comment in the hashed region changed)"},
+    "aniso1mm": {"source_sha": "9b1e26a920e49e63", "bytes": 2.93e9 + 3.38e9,
                  "note": "one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the "
-                         "standalone launch on this workload at full size"},
+                         "standalone launch on this workload at full size, on the same kernel code (a comment "
+                         "in the hashed region changed since)"},
 }
 
 

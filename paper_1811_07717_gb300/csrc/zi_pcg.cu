@@ -112,9 +112,10 @@ template <typename V> __device__ __forceinline__ V ldg_v(const V* p) { return __
 // columns in 8 bytes; every operation on them is FP32), so the SpMM gathers
 // half the bytes per stored entry and the vector updates move fewer.  x, r and
 // q = A p all use the stored direction, so the recurrences stay consistent;
-// only the choice of direction is rounded.  The residual recurrence keeps the
-// rounded r (its column dots are taken from the stored values), and the FP64
-// refinement replaces it by the true residual every phase.
+// only the choice of direction is rounded.  The residual recurrence continues
+// from the rounded r, while its column dots (r.w r and the stop test) take the
+// FP32 value before rounding; the FP64 refinement replaces r by the true
+// residual every phase.
 // Store<T>: storage of one element, and of the vector of W columns a thread
 // handles (Vec<T>).
 template <typename T> struct Store { using elem = T; using vec = typename Vec<T>::type; };
@@ -611,9 +612,7 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(256)
         V q = ldg_v(Qv + o), r = sget(Rv[o]);
 #pragma unroll
         for (int k = 0; k < W; ++k) vset(r, k, vget(r, k) - al[v][k] * vget(q, k));
-        const SV rs = spack(r);
-        Rv[o] = rs;
-        r = sget(rs);  // the dots of the residual as stored
+        Rv[o] = spack(r);  // stored rounded; the dots take the FP32 value before rounding
 #pragma unroll
         for (int k = 0; k < W; ++k) {
           const T rv = vget(r, k);
@@ -1271,11 +1270,11 @@ __global__ void k_prep_inner(int64_t n, int ld, const double* __restrict__ w, co
       const float wi = (float)w[i];
       float4 pold = keep_p ? sget(*reinterpret_cast<const uint2*>(p32 + e)) : make_float4(0.f, 0.f, 0.f, 0.f);
       const float po[4] = {pold.x, pold.y, pold.z, pold.w};
-      // the residual as stored (FP16): p and the dots start from it
-      const uint2 rs = spack(make_float4(r64[0] * gi[0], r64[1] * gi[1], r64[2] * gi[2], r64[3] * gi[3]));
-      const float4 rf = sget(rs);
-      const float r[4] = {rf.x, rf.y, rf.z, rf.w};
-      float pn[4];
+      // r is stored rounded (FP16); p and the dots start from the FP32 value
+      float r[4], pn[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r[k] = r64[k] * gi[k];
+      const uint2 rs = spack(make_float4(r[0], r[1], r[2], r[3]));
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         pn[k] = kp[k] ? po[k] * ratio[k] : wi * r[k];
@@ -2692,9 +2691,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_batched(const BatchHead<T>* __res
         V r = sget(Rc[i * nv]);
 #pragma unroll
         for (int u = 0; u < W; ++u) vset(r, u, vget(r, u) - al[u] * vget(q, u));
-        const typename Store<T>::vec rs = spack(r);
-        Rc[i * nv] = rs;
-        r = sget(rs);  // the dots of the residual as stored
+        Rc[i * nv] = spack(r);  // stored rounded; the dots take the FP32 value before rounding
 #pragma unroll
         for (int u = 0; u < W; ++u) {
           const T rv = vget(r, u);
